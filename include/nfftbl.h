@@ -1,0 +1,234 @@
+/*
+ * nfftbl -- nonequispaced fast Fourier transforms for bandlimited functions
+ * on one GB300 (sm_103a).
+ *
+ * The library evaluates the NFFT-like procedure for bandlimited functions of
+ * Kircheis & Potts (Algorithm 4.2, matrix form f = Psi F D_psihat fhat of
+ * Eq. 4.11), its adjoint D_psihat F^H Psi^T, and the classical NFFT
+ * (Algorithm 2.1, A ~ B F D of Eqs. 2.2-2.6) on the same inputs.
+ *
+ * Problem (Section 1, Eq. 1.1 and the statement opening Section 4): given
+ * samples fhat(k), k in I_M = [-M/2, M/2)^d, of the Fourier transform of a
+ * bandlimited f, approximate f(x_j) at nodes x_j in [-1/2, 1/2)^d, d = 1..3.
+ *
+ * Storage conventions (the paper leaves them open):
+ *   - complex values are interleaved (re, im): complex64 (float2) for
+ *     single-precision plans, complex128 (double2) for double-precision plans;
+ *   - fhat is centred and row-major with dimension 0 slowest: element k sits
+ *     at sum_t (k_t + M_t/2) * prod_{s>t} M_s; a batch of B vectors is
+ *     B contiguous blocks of prod_t M_t elements;
+ *   - nodes x are N x d row-major, float (single plans) or double (double
+ *     plans), each coordinate in [-1/2, 1/2);
+ *   - f (length N per batch entry) is in the caller's node order; a batch is
+ *     B contiguous blocks of N elements.
+ *
+ * Ownership: every pointer argument named *_dev is caller-owned device memory
+ * (for example a torch tensor's storage) that must stay valid until the call's
+ * work on the plan's stream has finished; the library never frees it.  The
+ * plan owns its own buffers (window factors, grid, sorted nodes, tile
+ * tables, scratch) and releases them in nfftbl_destroy.
+ *
+ * Errors: every entry point returns an nfftbl_status; NFFTBL_OK is 0.  On any
+ * other status the plan keeps its previous valid state and
+ * nfftbl_last_error(plan) describes the failure.  No C++ exception crosses
+ * this interface.  Work is enqueued asynchronously on the plan's stream;
+ * nfftbl_set_nodes is the only call that synchronises (it reads back a
+ * domain-check flag and the work-list size).
+ */
+#ifndef NFFTBL_H
+#define NFFTBL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nfftbl_plan_s* nfftbl_plan_t;
+
+typedef enum {
+    NFFTBL_OK = 0,
+    NFFTBL_EINVAL = 1,        /* invalid argument (sizes, NULL pointers)          */
+    NFFTBL_EDOMAIN = 2,       /* a node outside [-1/2, 1/2)^d or NaN              */
+    NFFTBL_EUNSUPPORTED = 3,  /* valid in the paper but not built (e.g. L not 2^p) */
+    NFFTBL_ENOMEM = 4,        /* device allocation failed                         */
+    NFFTBL_ECUDA = 5,         /* a CUDA runtime/driver call failed                */
+    NFFTBL_ESTATE = 6,        /* call order violated (e.g. forward before nodes)  */
+    NFFTBL_ETIMEOUT = 7,      /* a bounded device-side wait gave up               */
+    NFFTBL_EINTERNAL = 8      /* internal consistency check failed                */
+} nfftbl_status;
+
+/* Window functions of the class Phi_{m,L} (Section 3, Remark 3.1). */
+typedef enum {
+    NFFTBL_WIN_SINH = 0,   /* Eq. 3.4: sinh(beta sqrt(1-(Lx/m)^2)) / sinh(beta)          */
+    NFFTBL_WIN_CKB = 1,    /* continuous Kaiser-Bessel: (I0(beta sqrt(.)) - 1)/(I0(beta) - 1) */
+    NFFTBL_WIN_TABLE = 2   /* caller-supplied table on u = |Lx|/m in [0,1] (learned window) */
+} nfftbl_window;
+
+typedef enum {
+    NFFTBL_F64 = 0,        /* double everywhere                                           */
+    NFFTBL_F32 = 1,        /* float data and arithmetic; FP64-derived weights and twiddles */
+    NFFTBL_F32_COMP = 2    /* as F32 with compensated (Neumaier) accumulation of tap rows  */
+} nfftbl_precision;
+
+typedef enum {
+    NFFTBL_SHANNON = 0,    /* Algorithm 4.2: kernel psi = sinc(L pi x) phi(x), zero extension */
+    NFFTBL_CLASSIC = 1     /* Algorithm 2.1: periodized window phi_m                            */
+} nfftbl_method;
+
+typedef struct {
+    int precision;          /* nfftbl_precision; default NFFTBL_F32                       */
+    int method;             /* nfftbl_method; default NFFTBL_SHANNON                      */
+    double beta;            /* window shape; <= 0 selects the default: pi m (1 - 1/sigma)
+                               for SHANNON, 2 pi m (1 - 1/(2 sigma)) for CLASSIC            */
+    int batch;              /* B >= 1 transforms sharing the nodes; default 1             */
+    const double* table;    /* host pointer, NFFTBL_WIN_TABLE only: values g(u_i) at
+                               u_i = i/(table_len-1), i = 0..table_len-1, copied by the plan */
+    int table_len;          /* >= 3 for NFFTBL_WIN_TABLE                                  */
+    int tile[3];            /* node-binning tile shape in grid cells; 0 = default         */
+    int nodes_per_item;     /* nodes per (tile, chunk) work item; 0 = default             */
+} nfftbl_opts;
+
+/* Fill *opts with the defaults listed above. */
+void nfftbl_default_opts(nfftbl_opts* opts);
+
+/*
+ * Create a plan (Algorithm 4.2 step 0a / Algorithm 2.1 step 0a).
+ *   out    : receives the plan handle (NULL on failure);
+ *   d      : dimension, 1..3;
+ *   M      : host array of d even band sizes M_t >= 2 (|I_M| = prod M_t);
+ *   sigma  : oversampling factor >= 1; L_t = 2 ceil(ceil(sigma M_t)/2)
+ *            (M_sigma of Algorithm 2.1; L = M(1+lambda) in Algorithm 4.2);
+ *   m      : truncation parameter, window support [-m/L, m/L];
+ *   window : nfftbl_window;
+ *   opts   : NULL for defaults.
+ * Computes on the device, in FP64, the window transform psi_hat (phi_hat for
+ * CLASSIC) at k in I_{M_t} per dimension by Gauss-Legendre quadrature, and the
+ * diagonal D_psihat = diag(1/(|I_L| psi_hat(k))) of Eq. 4.9 (D of Eq. 2.2) in
+ * tensor-product form.  Runs on the legacy default stream and synchronises.
+ * Errors: EINVAL (d, M odd or < 2, sigma < 1, m < 1, 2m >= L_t, batch < 1,
+ * bad table or tile, beta <= 0 after defaults), EUNSUPPORTED (L_t not a
+ * power of two in [16, 4096], m outside 2..12, prod L_t >= 2^31, a box of
+ * tile plus halo beyond shared memory), ENOMEM, ECUDA.  The message of a
+ * failed call is available from nfftbl_plan_error().
+ */
+nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m,
+                          int window, const nfftbl_opts* opts);
+
+/* Enqueue all later work of this plan on cuda_stream (a cudaStream_t; NULL =
+ * legacy default stream).  Never fails for a valid plan. */
+nfftbl_status nfftbl_set_stream(nfftbl_plan_t plan, void* cuda_stream);
+
+/*
+ * Set the nodes x_j (Algorithm 4.2 inputs; index set J_{L,m}(x) of Eq. 4.8).
+ *   N     : number of nodes, 0 <= N < 2^31;
+ *   x_dev : N x d device array (float for F32/F32_COMP plans, double for F64),
+ *           row-major; may be freed by the caller once this call returns.
+ * Bins the nodes into grid tiles: cell i_t = floor(L_t x_t) + L_t/2, tile and
+ * in-tile cell key, stable order by (key, j), tile offsets and the work list.
+ * Synchronises the stream.  Errors: EINVAL, EDOMAIN (a coordinate outside
+ * [-1/2, 1/2) or NaN; the plan then has no nodes), ENOMEM, ECUDA.
+ */
+nfftbl_status nfftbl_set_nodes(nfftbl_plan_t plan, int64_t N, const void* x_dev);
+
+/*
+ * Forward transform f = Psi F D_psihat fhat (Eq. 4.11; Algorithm 4.2 steps
+ * 1-3), or f = B F D fhat for CLASSIC (Algorithm 2.1).
+ *   fhat_dev : B x prod(M_t) complex input (centred, row-major);
+ *   f_dev    : B x N complex output in the caller's node order.
+ * The plan's grid keeps the equispaced values vartheta_l (Eq. 4.7) until the
+ * next transform.  Asynchronous: errors: ESTATE (no nodes set), EINVAL
+ * (NULL), ECUDA (launch failure).  Device-side failures (a bounded wait on a
+ * tile copy that gave up) are reported by the next nfftbl_sync.
+ */
+nfftbl_status nfftbl_forward(nfftbl_plan_t plan, const void* fhat_dev, void* f_dev);
+
+/*
+ * Adjoint transform fhat = D_psihat F^H Psi^T f (the transpose of Eq. 4.11;
+ * the paper does not state it), or D F^H B^T f for CLASSIC.
+ *   f_dev    : B x N complex input in the caller's node order;
+ *   fhat_dev : B x prod(M_t) complex output (centred, row-major).
+ * The grid is overwritten.  Errors as for nfftbl_forward.
+ */
+nfftbl_status nfftbl_adjoint(nfftbl_plan_t plan, const void* f_dev, void* fhat_dev);
+
+/*
+ * Node gradient: gradx[j, t] = sum_b Re(conj(gradf[b, j]) * d f_{b,j} / d x_{j,t})
+ * for the forward map of this plan (not in the paper; the derivative of the
+ * short sums of Algorithm 4.2 step 3 with respect to the node).
+ *   fhat_dev  : B x prod(M_t) complex (the forward input);
+ *   gradf_dev : B x N complex (gradient with respect to f);
+ *   gradx_dev : N x d real output (float or double, the plan's precision).
+ * Recomputes the grid from fhat.  Errors as for nfftbl_forward.
+ */
+nfftbl_status nfftbl_node_grad(nfftbl_plan_t plan, const void* fhat_dev, const void* gradf_dev,
+                               void* gradx_dev);
+
+/* Wait for the plan's stream and report device-side failures of the work
+ * enqueued so far: ETIMEOUT if a bounded wait gave up (results invalid),
+ * EINTERNAL for another device error word; the word is cleared. */
+nfftbl_status nfftbl_sync(nfftbl_plan_t plan);
+
+/* Release the plan and all of its device memory.  NULL is accepted.  The
+ * handle must not be used again. */
+nfftbl_status nfftbl_destroy(nfftbl_plan_t plan);
+
+/* Text of the last error on this plan ("" if none; a static message for a NULL
+ * plan).  Valid until the next call on the plan. */
+const char* nfftbl_last_error(nfftbl_plan_t plan);
+
+/* Text of the last nfftbl_plan failure in this thread (the plan handle is NULL
+ * then). */
+const char* nfftbl_plan_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Introspection, for tests and benchmarks.  All copy to caller-owned HOST
+ * memory and synchronise the plan's stream.
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    int d, M[3], L[3], m, precision, method, window, batch;
+    double beta;
+    int tile[3];
+    int64_t n_nodes;
+    int64_t n_tiles;
+    int64_t n_work;         /* work items (tile, chunk) after set_nodes              */
+    int key_bits;           /* bits of the binning key                               */
+} nfftbl_info;
+
+nfftbl_status nfftbl_get_info(nfftbl_plan_t plan, nfftbl_info* info);
+
+/* Precorrection factors of dimension t: d_t(k) = 1/(L_t psi_hat_t(k)),
+ * k in I_{M_t} centred (M_t doubles), so that D = prod_t d_t (Eq. 4.9). */
+nfftbl_status nfftbl_get_factors(nfftbl_plan_t plan, int t, double* host_out);
+
+/* Binning results after set_nodes: keys (N uint32, sorted order), perm (N
+ * uint32, original index of each sorted node), tile_off (n_tiles+1 uint32).
+ * Any pointer may be NULL to skip it. */
+nfftbl_status nfftbl_get_binning(nfftbl_plan_t plan, uint32_t* keys, uint32_t* perm,
+                                 uint32_t* tile_off);
+
+/* Copy the current grid (B x prod(L_t) complex, centred) into host memory. */
+nfftbl_status nfftbl_get_grid(nfftbl_plan_t plan, void* host_out);
+
+/* Device address of the plan's grid (B x prod(L_t) complex, centred) so that
+ * a caller may run step 3 (or its adjoint) on a grid it filled itself. */
+nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t plan, void** grid_dev);
+
+/*
+ * Step 3 alone (Algorithm 4.2 step 3 / Algorithm 2.1 step 3): f = Psi grid
+ * from the plan's current grid, and its transpose grid = Psi^T f (the grid is
+ * cleared first).  For experiments that supply equispaced samples directly,
+ * such as the exponential approximations of Eqs. 5.1-5.2.
+ */
+nfftbl_status nfftbl_interp_grid(nfftbl_plan_t plan, void* f_dev);
+nfftbl_status nfftbl_spread_grid(nfftbl_plan_t plan, const void* f_dev);
+
+/* Number of this library's kernels launched on the plan so far (all calls). */
+int64_t nfftbl_kernel_launches(nfftbl_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFFTBL_H */

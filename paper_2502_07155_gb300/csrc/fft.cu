@@ -1,0 +1,255 @@
+// Steps 1-2 of Algorithm 4.2 (and of Algorithm 2.1) and their adjoint.
+//
+// Forward, one pass per dimension t = d-1, ..., 0 (pruned: only lines whose
+// input is nonzero are transformed, i.e. dimensions not yet transformed keep
+// their M_t extent):
+//   load   a[q] = fhat[k] * (-1)^k d_t(k) at q = k mod L_t for k in I_{M_t}, 0 elsewhere
+//          (the precorrection theta_hat = fhat / psi_hat of step 1 with the
+//          1/|I_L| of step 2, Eq. 4.9, and the centring shift l = s - L/2);
+//   FFT    vartheta[s] = sum_q a[q] e^{+2 pi i q s / L_t}   (inverse-sign DFT);
+//   store  all L_t outputs, centred index s = l + L_t/2.
+// Adjoint, t = 0, ..., d-1: load L_t values, forward-sign DFT, store only
+// k in I_{M_t} multiplied by (-1)^k d_t(k)  (F^H and D_psihat of Eq. 4.11).
+//
+// Each CTA transforms W lines of one pass in shared memory with a
+// mixed-radix (4, then 2) Stockham autosort FFT; twiddles come from an FP64
+// table rounded to the plan's precision.
+#include <algorithm>
+
+#include "plan_internal.h"
+
+namespace nfftbl {
+namespace {
+
+constexpr int kFftThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+    return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {   // a * conj(b)
+    return cmake<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+template <typename T, bool ADJ>
+__global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __restrict__ in, C2<T>* __restrict__ out,
+                                                               long long outer, int inner, int M, int L, int W,
+                                                               const T* __restrict__ fac,
+                                                               const C2<T>* __restrict__ tw) {
+    using CT = C2<T>;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int pitch = L + 1;
+    CT* bufA = reinterpret_cast<CT*>(sm_raw);
+    CT* bufB = bufA + W * pitch;
+    CT* twd = bufB + W * pitch;
+    const int tid = threadIdx.x;
+    for (int j = tid; j < L; j += blockDim.x) twd[j] = tw[j];
+
+    const int n_in = ADJ ? L : M;
+    const int n_out = ADJ ? M : L;
+    long long o0 = 0;
+    int i0 = 0, nl = W;
+    if (inner == 1) {
+        o0 = static_cast<long long>(blockIdx.x) * W;
+        nl = static_cast<int>((outer - o0 < W) ? (outer - o0) : W);
+    } else {
+        const int per = inner / W;
+        o0 = blockIdx.x / per;
+        i0 = (blockIdx.x % per) * W;
+    }
+
+    // ---- load
+    if (!ADJ) {
+        const int zlo = M / 2, zhi = L - M / 2;   // zero-padded positions [zlo, zhi)
+        for (int idx = tid; idx < W * (zhi - zlo); idx += blockDim.x) {
+            const int w = idx / (zhi - zlo);
+            bufA[w * pitch + zlo + idx % (zhi - zlo)] = cmake<T>(T(0), T(0));
+        }
+    }
+    for (int idx = tid; idx < W * n_in; idx += blockDim.x) {
+        int w, p;
+        long long g;
+        if (inner == 1) {
+            w = idx / n_in;
+            p = idx - w * n_in;
+            g = (o0 + w) * n_in + p;
+        } else {
+            p = idx / W;
+            w = idx - p * W;
+            g = (o0 * n_in + p) * static_cast<long long>(inner) + i0 + w;
+        }
+        CT v = cmake<T>(T(0), T(0));
+        if (w < nl) v = in[g];
+        int q = p;
+        if (!ADJ) {
+            const T f = fac[p];
+            v.x *= f;
+            v.y *= f;
+            q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+        }
+        bufA[w * pitch + q] = v;
+    }
+    __syncthreads();
+
+    // ---- Stockham stages: radix 4 while possible, then radix 2
+    CT* src = bufA;
+    CT* dst = bufB;
+    int span = 1;
+    while (span < L) {
+        const int r = (span * 4 <= L) ? 4 : 2;
+        const int nb = L / r;
+        const int tstep = L / (r * span);
+        for (int b = tid; b < W * nb; b += blockDim.x) {
+            const int w = b / nb;
+            const int i = b - w * nb;
+            const int k = i & (span - 1);
+            const CT* s = src + w * pitch;
+            CT* dd = dst + w * pitch;
+            const int obase = (i - k) * r + k;
+            if (r == 4) {
+                CT c0 = s[i], c1 = s[i + nb], c2 = s[i + 2 * nb], c3 = s[i + 3 * nb];
+                if (span > 1) {
+                    const int e = k * tstep;
+                    if (!ADJ) {
+                        c1 = cmul<T>(c1, twd[e & (L - 1)]);
+                        c2 = cmul<T>(c2, twd[(2 * e) & (L - 1)]);
+                        c3 = cmul<T>(c3, twd[(3 * e) & (L - 1)]);
+                    } else {
+                        c1 = cmulc<T>(c1, twd[e & (L - 1)]);
+                        c2 = cmulc<T>(c2, twd[(2 * e) & (L - 1)]);
+                        c3 = cmulc<T>(c3, twd[(3 * e) & (L - 1)]);
+                    }
+                }
+                const CT a0 = cmake<T>(c0.x + c2.x, c0.y + c2.y);
+                const CT a1 = cmake<T>(c0.x - c2.x, c0.y - c2.y);
+                const CT a2 = cmake<T>(c1.x + c3.x, c1.y + c3.y);
+                const CT dm = cmake<T>(c1.x - c3.x, c1.y - c3.y);
+                // a3 = (c1 - c3) * (s i), s = +1 forward (inverse DFT), -1 adjoint
+                const CT a3 = ADJ ? cmake<T>(dm.y, -dm.x) : cmake<T>(-dm.y, dm.x);
+                dd[obase] = cmake<T>(a0.x + a2.x, a0.y + a2.y);
+                dd[obase + span] = cmake<T>(a1.x + a3.x, a1.y + a3.y);
+                dd[obase + 2 * span] = cmake<T>(a0.x - a2.x, a0.y - a2.y);
+                dd[obase + 3 * span] = cmake<T>(a1.x - a3.x, a1.y - a3.y);
+            } else {
+                CT c0 = s[i], c1 = s[i + nb];
+                if (span > 1) {
+                    const int e = (k * tstep) & (L - 1);
+                    c1 = ADJ ? cmulc<T>(c1, twd[e]) : cmul<T>(c1, twd[e]);
+                }
+                dd[obase] = cmake<T>(c0.x + c1.x, c0.y + c1.y);
+                dd[obase + span] = cmake<T>(c0.x - c1.x, c0.y - c1.y);
+            }
+        }
+        __syncthreads();
+        CT* tmp = src;
+        src = dst;
+        dst = tmp;
+        span *= r;
+    }
+
+    // ---- store
+    for (int idx = tid; idx < W * n_out; idx += blockDim.x) {
+        int w, p;
+        long long g;
+        if (inner == 1) {
+            w = idx / n_out;
+            p = idx - w * n_out;
+            g = (o0 + w) * n_out + p;
+        } else {
+            p = idx / W;
+            w = idx - p * W;
+            g = (o0 * n_out + p) * static_cast<long long>(inner) + i0 + w;
+        }
+        if (w >= nl) continue;
+        CT v;
+        if (!ADJ) {
+            v = src[w * pitch + p];
+        } else {
+            const int q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+            v = src[w * pitch + q];
+            const T f = fac[p];
+            v.x *= f;
+            v.y *= f;
+        }
+        out[g] = v;
+    }
+}
+
+template <typename T>
+size_t fft_smem(int L, int W) {
+    return (2 * static_cast<size_t>(W) * (L + 1) + L) * sizeof(C2<T>);
+}
+
+template <typename T>
+int choose_lines(int L, long long inner) {
+    int W = 16;
+    while (W > 1 && fft_smem<T>(L, W) > 64 * 1024) W >>= 1;
+    if (inner > 1) W = static_cast<int>(std::min<long long>(W, inner));
+    return W;
+}
+
+template <typename T, bool ADJ>
+nfftbl_status run_pass(nfftbl_plan_s* p, const void* in, void* out, int t) {
+    long long outer = p->batch;
+    for (int s = 0; s < t; ++s) outer *= p->M[s];
+    long long inner = 1;
+    for (int s = t + 1; s < p->d; ++s) inner *= p->L[s];
+    const int L = p->L[t], M = p->M[t];
+    const int W = choose_lines<T>(L, inner);
+    const size_t smem = fft_smem<T>(L, W);
+    auto kern = fft_pass_kernel<T, ADJ>;
+    nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          static_cast<int>(smem)),
+                                  "fft smem attribute");
+    if (st != NFFTBL_OK) return st;
+    long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
+    kern<<<static_cast<unsigned>(blocks), kFftThreads, smem, p->stream>>>(
+        static_cast<const C2<T>*>(in), static_cast<C2<T>*>(out), outer, static_cast<int>(inner), M, L, W,
+        static_cast<const T*>(p->facT[t].p), static_cast<const C2<T>*>(p->tw[t].p));
+    p->launches++;
+    return check_cuda(p, cudaGetLastError(), "fft pass launch");
+}
+
+template <typename T>
+nfftbl_status forward_impl(nfftbl_plan_s* p, const void* fhat) {
+    const int d = p->d;
+    const void* src = fhat;
+    for (int t = d - 1; t >= 0; --t) {
+        void* dst = (t == 0) ? p->grid.p : ((t == d - 1) ? p->tmpA.p : p->tmpB.p);
+        nfftbl_status st = run_pass<T, false>(p, src, dst, t);
+        if (st != NFFTBL_OK) return st;
+        src = dst;
+    }
+    return NFFTBL_OK;
+}
+
+template <typename T>
+nfftbl_status adjoint_impl(nfftbl_plan_s* p, void* fhat) {
+    const int d = p->d;
+    const void* src = p->grid.p;
+    for (int t = 0; t < d; ++t) {
+        void* dst = (t == d - 1) ? fhat : ((t == 0) ? p->tmpB.p : p->tmpA.p);
+        if (d == 2 && t == 0) dst = p->tmpA.p;
+        nfftbl_status st = run_pass<T, true>(p, src, dst, t);
+        if (st != NFFTBL_OK) return st;
+        src = dst;
+    }
+    return NFFTBL_OK;
+}
+
+}  // namespace
+
+// Scratch layout: d = 2 uses tmpA (B M0 L1); d = 3 uses tmpA (B M0 M1 L2)
+// and tmpB (B M0 L1 L2).
+nfftbl_status fft_forward(nfftbl_plan_s* p, const void* fhat) {
+    if (p->precision == NFFTBL_F64) return forward_impl<double>(p, fhat);
+    return forward_impl<float>(p, fhat);
+}
+
+nfftbl_status fft_adjoint(nfftbl_plan_s* p, void* fhat) {
+    if (p->precision == NFFTBL_F64) return adjoint_impl<double>(p, fhat);
+    return adjoint_impl<float>(p, fhat);
+}
+
+}  // namespace nfftbl

@@ -1,0 +1,565 @@
+// C-ABI entry points (include/nfftbl.h): plan creation and validation, the
+// TMA descriptor of the grid, and the order of kernels per transform.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "plan_internal.h"
+
+namespace nfftbl {
+
+namespace {
+thread_local std::string g_plan_error;
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+    int r = 0;
+    while ((1LL << r) < v) ++r;
+    return r;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+size_t complex_bytes(const nfftbl_plan_s* p) { return p->precision == NFFTBL_F64 ? 16 : 8; }
+
+long long prod_L(const nfftbl_plan_s* p) {
+    long long s = 1;
+    for (int t = 0; t < p->d; ++t) s *= p->L[t];
+    return s;
+}
+
+long long box_cells(const TileGeom& g) {
+    long long c = 1;
+    for (int t = 0; t < g.d; ++t) c *= g.box[t];
+    return c;
+}
+
+void set_geom(TileGeom& g, int d, const int* L, const int* T, int m) {
+    g.d = d;
+    g.cells_per_tile_log2 = 0;
+    for (int t = 0; t < 3; ++t) {
+        g.L[t] = (t < d) ? L[t] : 1;
+        g.T[t] = (t < d) ? T[t] : 1;
+        g.nt[t] = g.L[t] / g.T[t];
+        if (t < d) {
+            // fastest dimension: origin kept even (16-byte TMA start for float2)
+            const bool fast = (t == d - 1);
+            g.off[t] = fast ? ((m & 1) ? m - 1 : m) : m - 1;
+            g.box[t] = g.T[t] + 2 * m - (fast ? 0 : 1);
+            g.cells_per_tile_log2 += ilog2(g.T[t]);
+        } else {
+            g.off[t] = 0;
+            g.box[t] = 1;
+        }
+    }
+}
+
+constexpr size_t kBoxBudget = 96 * 1024;   // per CTA, leaves room for 2 CTAs/SM
+constexpr size_t kBoxMax = 200 * 1024;     // hard cap on one box
+
+nfftbl_status make_tmap(nfftbl_plan_s* p) {
+    auto fn = encode_fn();
+    if (!fn) return fail(p, NFFTBL_ECUDA, "cuTensorMapEncodeTiled entry point not available");
+    const int d = p->d;
+    const int rank = d + 1;
+    const size_t es = (p->precision == NFFTBL_F64) ? 8 : 4;
+    cuuint64_t dims[5];
+    cuuint64_t strides[4];
+    cuuint32_t box[5];
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    dims[0] = 2ull * p->L[d - 1];
+    box[0] = 2u * p->geom.box[d - 1];
+    for (int r = 1; r < d; ++r) {
+        dims[r] = p->L[d - 1 - r];
+        box[r] = p->geom.box[d - 1 - r];
+    }
+    dims[d] = p->batch;
+    box[d] = 1;
+    cuuint64_t st = dims[0] * es;
+    for (int r = 1; r < rank; ++r) {
+        strides[r - 1] = st;
+        st *= dims[r];
+    }
+    CUresult res = fn(&p->tmap, p->precision == NFFTBL_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                      rank, p->grid.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (res != CUDA_SUCCESS) return fail(p, NFFTBL_ECUDA, "cuTensorMapEncodeTiled failed");
+    p->tmap_ok = true;
+    return NFFTBL_OK;
+}
+
+template <typename T>
+TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
+    TapArgs<T> a{};
+    a.g = p->geom;
+    a.w.method = p->method;
+    a.w.window = p->window;
+    a.w.m = p->m;
+    a.w.inv_m = static_cast<T>(1.0 / p->m);
+    a.w.beta = static_cast<T>(p->beta);
+    a.w.c_exp = static_cast<T>(p->beta / std::log(2.0));
+    if (p->window == NFFTBL_WIN_SINH)
+        a.w.c_norm = static_cast<T>(1.0 / -std::expm1(-2.0 * p->beta));
+    else if (p->window == NFFTBL_WIN_CKB)
+        a.w.c_norm = static_cast<T>(1.0 / (std::cyl_bessel_i(0.0, p->beta) - 1.0));
+    else
+        a.w.c_norm = T(1);
+    a.w.table = static_cast<const T*>(p->window == NFFTBL_WIN_TABLE ? p->table_dev.p : nullptr);
+    a.w.table_n = static_cast<int>(p->table_host.size()) - 1;
+    a.batch = p->batch;
+    const size_t bb = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
+    a.batch_smem = static_cast<int>(std::max<size_t>(1, std::min<size_t>(p->batch, kBoxBudget / bb)));
+    a.comp = p->precision == NFFTBL_F32_COMP;
+    a.xs = static_cast<const T*>(p->xs.p);
+    a.perm = static_cast<const uint32_t*>(p->perm.p);
+    a.work = static_cast<const WorkItem*>(p->work.p);
+    a.n_work = static_cast<int>(p->n_work);
+    a.N = p->N;
+    a.grid = static_cast<C2<T>*>(p->grid.p);
+    a.grid_stride = prod_L(p);
+    a.err = static_cast<int*>(p->err.p);
+    return a;
+}
+
+template <typename T>
+nfftbl_status run_taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, void* gradx) {
+    TapArgs<T> a = make_tap_args<T>(p);
+    a.fin = static_cast<const C2<T>*>(fin);
+    a.fout = static_cast<C2<T>*>(fout);
+    a.gradx = static_cast<T*>(gradx);
+    // box slots padded to 128 bytes, plus 128 bytes to align the base
+    const size_t slot = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
+    const size_t smem = static_cast<size_t>(a.batch_smem) * slot + 128;
+    switch (p->d) {
+        case 1: return run_taps_d<T, 1>(p, a, kind, smem);
+        case 2: return run_taps_d<T, 2>(p, a, kind, smem);
+        default: return run_taps_d<T, 3>(p, a, kind, smem);
+    }
+}
+
+nfftbl_status taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, void* gradx) {
+    if (p->precision == NFFTBL_F64) return run_taps<double>(p, kind, fin, fout, gradx);
+    return run_taps<float>(p, kind, fin, fout, gradx);
+}
+
+void destroy_plan(nfftbl_plan_s* p) {
+    if (!p) return;
+    free_buf(p->table_dev);
+    free_buf(p->table_dev64);
+    for (int t = 0; t < 3; ++t) {
+        free_buf(p->fac64[t]);
+        free_buf(p->facT[t]);
+        free_buf(p->tw[t]);
+    }
+    free_buf(p->grid);
+    free_buf(p->tmpA);
+    free_buf(p->tmpB);
+    free_buf(p->xs);
+    free_buf(p->keys);
+    free_buf(p->perm);
+    free_buf(p->keys_tmp);
+    free_buf(p->perm_tmp);
+    free_buf(p->hist);
+    free_buf(p->tile_off);
+    free_buf(p->work);
+    free_buf(p->counters);
+    free_buf(p->err);
+    if (p->err_host) cudaFreeHost(p->err_host);
+    delete p;
+}
+
+// Record the failure of nfftbl_plan (msg, or the plan's own message when
+// msg is empty) and release the partly built plan.
+nfftbl_status plan_fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& msg) {
+    g_plan_error = (msg.empty() && p) ? p->last_error : msg;
+    destroy_plan(p);
+    return st;
+}
+
+}  // namespace
+
+nfftbl_status fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& msg) {
+    if (p) p->last_error = msg;
+    return st;
+}
+
+nfftbl_status check_cuda(nfftbl_plan_s* p, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return NFFTBL_OK;
+    cudaGetLastError();   // clear a sticky launch error of this thread
+    const std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(p, e == cudaErrorMemoryAllocation ? NFFTBL_ENOMEM : NFFTBL_ECUDA, msg);
+}
+
+nfftbl_status ensure_buf(nfftbl_plan_s* p, DeviceBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return NFFTBL_OK;
+    free_buf(b);
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(p, NFFTBL_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+    }
+    b.p = ptr;
+    b.bytes = bytes;
+    return NFFTBL_OK;
+}
+
+void free_buf(DeviceBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+}  // namespace nfftbl
+
+using namespace nfftbl;
+
+extern "C" {
+
+void nfftbl_default_opts(nfftbl_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = NFFTBL_F32;
+    o->method = NFFTBL_SHANNON;
+    o->beta = 0.0;
+    o->batch = 1;
+}
+
+nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m, int window,
+                          const nfftbl_opts* opts) {
+    g_plan_error.clear();
+    if (!out) return plan_fail(nullptr, NFFTBL_EINVAL, "out is NULL");
+    *out = nullptr;
+    nfftbl_opts o;
+    nfftbl_default_opts(&o);
+    if (opts) o = *opts;
+    if (d < 1 || d > 3) return plan_fail(nullptr, NFFTBL_EINVAL, "d must be 1, 2 or 3");
+    if (!M) return plan_fail(nullptr, NFFTBL_EINVAL, "M is NULL");
+    if (!(sigma >= 1.0) || !std::isfinite(sigma)) return plan_fail(nullptr, NFFTBL_EINVAL, "sigma must be >= 1");
+    if (m < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "m must be >= 1");
+    if (window < 0 || window > 2) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown window");
+    if (o.precision < 0 || o.precision > 2) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown precision");
+    if (o.method < 0 || o.method > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown method");
+    if (o.batch < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "batch must be >= 1");
+    if (window == NFFTBL_WIN_TABLE && (!o.table || o.table_len < 3))
+        return plan_fail(nullptr, NFFTBL_EINVAL, "table window needs a table of >= 3 values");
+    if (o.nodes_per_item < 0) return plan_fail(nullptr, NFFTBL_EINVAL, "nodes_per_item must be >= 0");
+    int L[3] = {1, 1, 1};
+    for (int t = 0; t < d; ++t) {
+        if (M[t] < 2 || (M[t] & 1)) return plan_fail(nullptr, NFFTBL_EINVAL, "each M_t must be even and >= 2");
+        const long long s = static_cast<long long>(std::ceil(sigma * M[t] - 1e-9));
+        L[t] = static_cast<int>(2 * ((s + 1) / 2));
+        if (2 * m >= L[t]) return plan_fail(nullptr, NFFTBL_EINVAL, "2m must be < L_t");
+    }
+    for (int t = 0; t < d; ++t)
+        if (!is_pow2(L[t]) || L[t] < 16 || L[t] > 4096)
+            return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "L_t must be a power of two in [16, 4096]");
+    if (m < 2 || m > 12) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "m must be in 2..12");
+    double beta = o.beta;
+    if (!(beta > 0.0)) {
+        beta = (o.method == NFFTBL_SHANNON) ? M_PI * m * (1.0 - 1.0 / sigma)
+                                            : 2.0 * M_PI * m * (1.0 - 1.0 / (2.0 * sigma));
+        if (window == NFFTBL_WIN_TABLE) beta = 1.0;   // unused by a tabulated window
+    }
+    if (!(beta > 0.0)) return plan_fail(nullptr, NFFTBL_EINVAL, "beta must be > 0 (sigma = 1 needs an explicit beta)");
+    int key_bits = 0;
+    for (int t = 0; t < d; ++t) key_bits += ilog2(L[t]);
+    if (key_bits > 31) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "prod L_t must be < 2^31");
+
+    // tile shape
+    const int def_tile = (d == 1) ? 64 : (d == 2) ? 32 : 8;
+    int T[3] = {1, 1, 1};
+    const bool user_tile = o.tile[0] > 0;
+    for (int t = 0; t < d; ++t) {
+        T[t] = user_tile ? o.tile[t] : std::min(def_tile, L[t]);
+        if (!is_pow2(T[t]) || T[t] < 2 || L[t] % T[t] != 0)
+            return plan_fail(nullptr, NFFTBL_EINVAL, "tile extents must be powers of two >= 2 dividing L_t");
+    }
+    const size_t cb = (o.precision == NFFTBL_F64) ? 16 : 8;
+    TileGeom g{};
+    while (true) {
+        set_geom(g, d, L, T, m);
+        const size_t bytes = static_cast<size_t>(box_cells(g)) * cb;
+        const bool tma_ok = 2 * g.box[d - 1] <= 256 && (d < 2 || g.box[0] <= 256) && (d < 3 || g.box[1] <= 256);
+        if (bytes <= kBoxMax && tma_ok) break;
+        if (user_tile) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "tile box exceeds shared memory or TMA limits");
+        int big = 0;
+        for (int t = 1; t < d; ++t)
+            if (T[t] > T[big]) big = t;
+        if (T[big] <= 2) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "m too large for a shared-memory box");
+        T[big] /= 2;
+    }
+
+    nfftbl_plan_s* p = new (std::nothrow) nfftbl_plan_s();
+    if (!p) return plan_fail(nullptr, NFFTBL_ENOMEM, "host allocation failed");
+    p->d = d;
+    for (int t = 0; t < d; ++t) {
+        p->M[t] = M[t];
+        p->L[t] = L[t];
+    }
+    p->m = m;
+    p->sigma = sigma;
+    p->window = window;
+    p->method = o.method;
+    p->precision = o.precision;
+    p->beta = beta;
+    p->batch = o.batch;
+    p->nodes_per_item = o.nodes_per_item > 0 ? o.nodes_per_item : 1024;
+    p->geom = g;
+    p->key_bits = key_bits;
+    p->n_tiles = 1;
+    for (int t = 0; t < d; ++t) p->n_tiles *= g.nt[t];
+    if (window == NFFTBL_WIN_TABLE) p->table_host.assign(o.table, o.table + o.table_len);
+
+    nfftbl_status st;
+    if ((st = check_cuda(p, cudaGetDevice(&p->device), "cudaGetDevice")) != NFFTBL_OK) return plan_fail(p, st, "");
+    if ((st = check_cuda(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device),
+                         "SM count")) != NFFTBL_OK)
+        return plan_fail(p, st, "");
+    if ((st = ensure_buf(p, p->err, sizeof(int))) != NFFTBL_OK) return plan_fail(p, st, "");
+    if ((st = check_cuda(p, cudaMallocHost(reinterpret_cast<void**>(&p->err_host), sizeof(int)), "pinned err")) !=
+        NFFTBL_OK)
+        return plan_fail(p, st, "");
+    *p->err_host = 0;
+    cudaStream_t s0 = nullptr;
+    if ((st = check_cuda(p, cudaMemsetAsync(p->err.p, 0, sizeof(int), s0), "memset err")) != NFFTBL_OK)
+        return plan_fail(p, st, "");
+
+    const bool dbl = p->precision == NFFTBL_F64;
+    const double* tab64 = nullptr;
+    int tab_n = 0;
+    if (window == NFFTBL_WIN_TABLE) {
+        const size_t n = p->table_host.size();
+        tab_n = static_cast<int>(n) - 1;
+        if ((st = ensure_buf(p, p->table_dev64, n * sizeof(double))) != NFFTBL_OK) return plan_fail(p, st, "");
+        if ((st = check_cuda(p, cudaMemcpy(p->table_dev64.p, p->table_host.data(), n * sizeof(double),
+                                           cudaMemcpyHostToDevice),
+                             "table upload")) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+        tab64 = static_cast<const double*>(p->table_dev64.p);
+        if (dbl) {
+            p->table_dev = p->table_dev64;   // shared, freed once below
+            p->table_dev64 = DeviceBuf{};
+            tab64 = static_cast<const double*>(p->table_dev.p);
+        } else {
+            if ((st = ensure_buf(p, p->table_dev, n * sizeof(float))) != NFFTBL_OK) return plan_fail(p, st, "");
+            if ((st = check_cuda(p, launch_table_cast(tab64, static_cast<int>(n), static_cast<float*>(p->table_dev.p),
+                                                      s0),
+                                 "table cast")) != NFFTBL_OK)
+                return plan_fail(p, st, "");
+        }
+    }
+    for (int t = 0; t < d; ++t) {
+        if ((st = ensure_buf(p, p->fac64[t], M[t] * sizeof(double))) != NFFTBL_OK) return plan_fail(p, st, "");
+        if ((st = ensure_buf(p, p->facT[t], M[t] * (dbl ? 8 : 4))) != NFFTBL_OK) return plan_fail(p, st, "");
+        if ((st = ensure_buf(p, p->tw[t], L[t] * complex_bytes(p))) != NFFTBL_OK) return plan_fail(p, st, "");
+        if ((st = check_cuda(p, launch_window_factors(p->method == NFFTBL_SHANNON, window, L[t], M[t], m, beta,
+                                                      tab64, tab_n, static_cast<double*>(p->fac64[t].p), s0),
+                             "window factors")) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+        if ((st = check_cuda(p, launch_cast_factors(static_cast<double*>(p->fac64[t].p), M[t], p->facT[t].p, dbl, s0),
+                             "factor cast")) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+        if ((st = check_cuda(p, launch_twiddles(L[t], p->tw[t].p, dbl, s0), "twiddles")) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+        p->launches += 3;
+    }
+    const long long B = p->batch;
+    const size_t cbytes = complex_bytes(p);
+    if ((st = ensure_buf(p, p->grid, B * prod_L(p) * cbytes)) != NFFTBL_OK) return plan_fail(p, st, "");
+    if (d == 2) {
+        if ((st = ensure_buf(p, p->tmpA, B * static_cast<long long>(M[0]) * L[1] * cbytes)) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+    } else if (d == 3) {
+        if ((st = ensure_buf(p, p->tmpA, B * static_cast<long long>(M[0]) * M[1] * L[2] * cbytes)) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+        if ((st = ensure_buf(p, p->tmpB, B * static_cast<long long>(M[0]) * L[1] * L[2] * cbytes)) != NFFTBL_OK)
+            return plan_fail(p, st, "");
+    }
+    if ((st = check_cuda(p, cudaMemsetAsync(p->grid.p, 0, B * prod_L(p) * cbytes, s0), "grid clear")) != NFFTBL_OK)
+        return plan_fail(p, st, "");
+    if ((st = make_tmap(p)) != NFFTBL_OK) return plan_fail(p, st, "");
+    if ((st = check_cuda(p, cudaStreamSynchronize(s0), "plan sync")) != NFFTBL_OK) return plan_fail(p, st, "");
+    *out = p;
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_set_stream(nfftbl_plan_t p, void* stream) {
+    if (!p) return NFFTBL_EINVAL;
+    p->stream = static_cast<cudaStream_t>(stream);
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_set_nodes(nfftbl_plan_t p, int64_t N, const void* x_dev) {
+    if (!p) return NFFTBL_EINVAL;
+    if (N < 0 || N >= (1LL << 31)) return fail(p, NFFTBL_EINVAL, "N must be in [0, 2^31)");
+    if (N > 0 && !x_dev) return fail(p, NFFTBL_EINVAL, "x_dev is NULL");
+    p->last_error.clear();
+    return bin_nodes(p, N, x_dev);
+}
+
+static nfftbl_status ready(nfftbl_plan_t p) {
+    if (!p) return NFFTBL_EINVAL;
+    if (p->N < 0) return fail(p, NFFTBL_ESTATE, "nodes not set (nfftbl_set_nodes)");
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_forward(nfftbl_plan_t p, const void* fhat_dev, void* f_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_dev || (!f_dev && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    if ((st = fft_forward(p, fhat_dev)) != NFFTBL_OK) return st;
+    return taps(p, TAP_INTERP, nullptr, f_dev, nullptr);
+}
+
+nfftbl_status nfftbl_adjoint(nfftbl_plan_t p, const void* f_dev, void* fhat_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_dev || (!f_dev && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    const size_t bytes = static_cast<size_t>(p->batch) * prod_L(p) * complex_bytes(p);
+    if ((st = check_cuda(p, cudaMemsetAsync(p->grid.p, 0, bytes, p->stream), "grid clear")) != NFFTBL_OK) return st;
+    if ((st = taps(p, TAP_SPREAD, f_dev, nullptr, nullptr)) != NFFTBL_OK) return st;
+    return fft_adjoint(p, fhat_dev);
+}
+
+nfftbl_status nfftbl_node_grad(nfftbl_plan_t p, const void* fhat_dev, const void* gradf_dev, void* gradx_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_dev || ((!gradf_dev || !gradx_dev) && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    if ((st = fft_forward(p, fhat_dev)) != NFFTBL_OK) return st;
+    return taps(p, TAP_GRAD, gradf_dev, nullptr, gradx_dev);
+}
+
+nfftbl_status nfftbl_interp_grid(nfftbl_plan_t p, void* f_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!f_dev && p->N > 0) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    return taps(p, TAP_INTERP, nullptr, f_dev, nullptr);
+}
+
+nfftbl_status nfftbl_spread_grid(nfftbl_plan_t p, const void* f_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!f_dev && p->N > 0) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    const size_t bytes = static_cast<size_t>(p->batch) * prod_L(p) * complex_bytes(p);
+    if ((st = check_cuda(p, cudaMemsetAsync(p->grid.p, 0, bytes, p->stream), "grid clear")) != NFFTBL_OK) return st;
+    return taps(p, TAP_SPREAD, f_dev, nullptr, nullptr);
+}
+
+nfftbl_status nfftbl_sync(nfftbl_plan_t p) {
+    if (!p) return NFFTBL_EINVAL;
+    nfftbl_status st;
+    if ((st = check_cuda(p, cudaMemcpyAsync(p->err_host, p->err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream),
+                         "read err")) != NFFTBL_OK)
+        return st;
+    if ((st = check_cuda(p, cudaStreamSynchronize(p->stream), "stream sync")) != NFFTBL_OK) return st;
+    const int e = *p->err_host;
+    if (e) {
+        cudaMemsetAsync(p->err.p, 0, sizeof(int), p->stream);
+        cudaStreamSynchronize(p->stream);
+        if (e & DEVERR_TIMEOUT) return fail(p, NFFTBL_ETIMEOUT, "a bounded device wait gave up");
+        return fail(p, NFFTBL_EINTERNAL, "device error word set");
+    }
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_destroy(nfftbl_plan_t p) {
+    if (!p) return NFFTBL_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    destroy_plan(p);
+    return NFFTBL_OK;
+}
+
+const char* nfftbl_last_error(nfftbl_plan_t p) {
+    if (!p) return "NULL plan";
+    return p->last_error.c_str();
+}
+
+const char* nfftbl_plan_error(void) { return g_plan_error.c_str(); }
+
+nfftbl_status nfftbl_get_info(nfftbl_plan_t p, nfftbl_info* info) {
+    if (!p || !info) return NFFTBL_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->d = p->d;
+    for (int t = 0; t < 3; ++t) {
+        info->M[t] = p->M[t];
+        info->L[t] = p->L[t];
+        info->tile[t] = p->geom.T[t];
+    }
+    info->m = p->m;
+    info->precision = p->precision;
+    info->method = p->method;
+    info->window = p->window;
+    info->batch = p->batch;
+    info->beta = p->beta;
+    info->n_nodes = p->N;
+    info->n_tiles = p->n_tiles;
+    info->n_work = p->n_work;
+    info->key_bits = p->key_bits;
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_get_factors(nfftbl_plan_t p, int t, double* host_out) {
+    if (!p || !host_out || t < 0 || t >= p->d) return NFFTBL_EINVAL;
+    nfftbl_status st = check_cuda(p, cudaMemcpyAsync(host_out, p->fac64[t].p, p->M[t] * sizeof(double),
+                                                     cudaMemcpyDeviceToHost, p->stream),
+                                  "copy factors");
+    if (st != NFFTBL_OK) return st;
+    return check_cuda(p, cudaStreamSynchronize(p->stream), "sync");
+}
+
+nfftbl_status nfftbl_get_binning(nfftbl_plan_t p, uint32_t* keys, uint32_t* perm, uint32_t* tile_off) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    const size_t n = static_cast<size_t>(p->N) * 4;
+    if (keys && n && (st = check_cuda(p, cudaMemcpyAsync(keys, p->keys.p, n, cudaMemcpyDeviceToHost, p->stream),
+                                      "copy keys")) != NFFTBL_OK)
+        return st;
+    if (perm && n && (st = check_cuda(p, cudaMemcpyAsync(perm, p->perm.p, n, cudaMemcpyDeviceToHost, p->stream),
+                                      "copy perm")) != NFFTBL_OK)
+        return st;
+    if (tile_off && (st = check_cuda(p, cudaMemcpyAsync(tile_off, p->tile_off.p, (p->n_tiles + 1) * 4,
+                                                        cudaMemcpyDeviceToHost, p->stream),
+                                     "copy tile_off")) != NFFTBL_OK)
+        return st;
+    return check_cuda(p, cudaStreamSynchronize(p->stream), "sync");
+}
+
+nfftbl_status nfftbl_get_grid(nfftbl_plan_t p, void* host_out) {
+    if (!p || !host_out) return NFFTBL_EINVAL;
+    const size_t bytes = static_cast<size_t>(p->batch) * prod_L(p) * complex_bytes(p);
+    nfftbl_status st =
+        check_cuda(p, cudaMemcpyAsync(host_out, p->grid.p, bytes, cudaMemcpyDeviceToHost, p->stream), "copy grid");
+    if (st != NFFTBL_OK) return st;
+    return check_cuda(p, cudaStreamSynchronize(p->stream), "sync");
+}
+
+nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t p, void** grid_dev) {
+    if (!p || !grid_dev) return NFFTBL_EINVAL;
+    *grid_dev = p->grid.p;
+    return NFFTBL_OK;
+}
+
+int64_t nfftbl_kernel_launches(nfftbl_plan_t p) { return p ? p->launches : 0; }
+
+}  // extern "C"

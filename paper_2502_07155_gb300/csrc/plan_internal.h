@@ -1,0 +1,152 @@
+// Host-side plan object and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nfftbl.h"
+#include "common.cuh"
+
+namespace nfftbl {
+
+// Parameters of the window / kernel evaluation, shared by all tap kernels.
+template <typename T>
+struct WinParams {
+    int method;        // NFFTBL_SHANNON / NFFTBL_CLASSIC
+    int window;        // nfftbl_window
+    int m;
+    T inv_m;           // 1/m
+    T beta;
+    T c_exp;           // beta / ln 2 (sinh window, exp2 form)
+    T c_norm;          // 1 / (1 - e^{-2 beta}) (sinh) or 1/(I0(beta) - 1) (cKB)
+    const T* table;    // window table on u in [0, 1] (table window), device
+    int table_n;       // number of intervals (table has table_n + 1 values)
+};
+
+// Geometry of the node tiles and of the shared-memory boxes around them.
+struct TileGeom {
+    int d;
+    int L[3];
+    int T[3];          // tile extent (cells)
+    int nt[3];         // tiles per dimension
+    int box[3];        // box extent (cells) per dimension
+    int off[3];        // box origin = tile origin - off
+    int cells_per_tile_log2;
+};
+
+template <typename T>
+struct TapArgs {
+    TileGeom g;
+    WinParams<T> w;
+    int batch;
+    int batch_smem;            // batch entries held in shared memory at once
+    int comp;                  // compensated accumulation (F32_COMP)
+    const T* xs;               // sorted nodes, N x d
+    const uint32_t* perm;      // sorted -> caller index
+    const WorkItem* work;
+    int n_work;
+    long long N;
+    C2<T>* grid;               // B x prod(L)
+    long long grid_stride;     // prod(L)
+    const C2<T>* fin;          // B x N (spread / grad input)
+    C2<T>* fout;               // B x N (interp output)
+    T* gradx;                  // N x d (node gradient output)
+    int* err;
+};
+
+struct DeviceBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace nfftbl
+
+struct nfftbl_plan_s {
+    int d = 0;
+    int M[3] = {1, 1, 1};
+    int L[3] = {1, 1, 1};
+    int m = 0;
+    double sigma = 2.0;
+    int window = NFFTBL_WIN_SINH;
+    int method = NFFTBL_SHANNON;
+    int precision = NFFTBL_F32;
+    double beta = 0.0;
+    int batch = 1;
+    int nodes_per_item = 0;
+    nfftbl::TileGeom geom{};
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    long long launches = 0;
+
+    // window
+    std::vector<double> table_host;
+    nfftbl::DeviceBuf table_dev;          // T (float or double) table values
+    nfftbl::DeviceBuf table_dev64;        // double copy for the quadrature
+    nfftbl::DeviceBuf fac64[3];           // d_t(k) = 1/(L psi_hat(k)), double, M_t entries
+    nfftbl::DeviceBuf facT[3];            // (-1)^k d_t(k), plan precision
+    nfftbl::DeviceBuf tw[3];              // twiddles e^{2 pi i j / L_t}, plan precision
+
+    // grid and FFT scratch
+    nfftbl::DeviceBuf grid;
+    nfftbl::DeviceBuf tmpA, tmpB;
+    CUtensorMap tmap{};
+    bool tmap_ok = false;
+
+    // nodes
+    long long N = -1;                     // -1: no nodes set
+    nfftbl::DeviceBuf xs;                 // sorted nodes
+    nfftbl::DeviceBuf keys, perm;         // sorted keys / permutation (uint32)
+    nfftbl::DeviceBuf keys_tmp, perm_tmp; // radix sort ping-pong
+    nfftbl::DeviceBuf hist;               // radix sort block histograms
+    nfftbl::DeviceBuf tile_off;           // n_tiles + 1 (uint32)
+    nfftbl::DeviceBuf work;               // WorkItem list
+    nfftbl::DeviceBuf counters;           // small device scratch (ints)
+    long long n_tiles = 0;
+    long long n_work = 0;
+    int key_bits = 0;
+
+    nfftbl::DeviceBuf err;                // device error word
+    int* err_host = nullptr;              // pinned mirror
+};
+
+namespace nfftbl {
+
+// Allocation helpers (plan.cu).
+nfftbl_status ensure_buf(nfftbl_plan_s* p, DeviceBuf& b, size_t bytes);
+void free_buf(DeviceBuf& b);
+nfftbl_status fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& msg);
+nfftbl_status check_cuda(nfftbl_plan_s* p, cudaError_t e, const char* what);
+
+// window.cu
+cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m, double beta,
+                                  const double* table, int table_n, double* fac64_out,
+                                  cudaStream_t s);
+cudaError_t launch_cast_factors(const double* fac64, int M, void* out, int is_double, cudaStream_t s);
+cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s);
+cudaError_t launch_table_cast(const double* in, int n, float* out, cudaStream_t s);
+
+// bin.cu
+nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev);
+
+// fft.cu
+nfftbl_status fft_forward(nfftbl_plan_s* p, const void* fhat);
+nfftbl_status fft_adjoint(nfftbl_plan_s* p, void* fhat);
+
+// Short-sum kernels (taps.cuh).  launch_tap_kernel is instantiated once per
+// (precision, dimension, tap count W = 2m, or W = 0 for m read at run time)
+// in translation units the build generates; taps_dispatch.cu picks one.
+enum TapKind { TAP_INTERP = 0, TAP_SPREAD = 1, TAP_GRAD = 2 };
+template <typename T, int D, int W>
+nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem);
+template <typename T, int D>
+nfftbl_status run_taps_d(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem);
+// Compile-time tap counts W = 2m built by the generator (others use W = 0).
+#define NFFTBL_FIXED_M_LIST(X) X(2) X(3) X(4) X(5) X(6) X(8)
+
+}  // namespace nfftbl

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every function include/nfftbl.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2502_07155_gb300 as nb
+from paper_2502_07155_gb300 import build as nbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(nfftbl_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return nbuild.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["nfftbl_plan", "nfftbl_set_nodes", "nfftbl_forward", "nfftbl_adjoint", "nfftbl_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding wraps exactly what the header declares
+    assert sorted(nb.EXPORTED) == declared_functions()
+
+
+def test_no_gpu_calls_fail_cleanly_on_host(libpath):
+    """Argument validation runs before any device work."""
+    lib = nb.lib()
+    h = ctypes.c_void_p()
+    M = (ctypes.c_int * 3)(256, 0, 0)
+    assert lib.nfftbl_plan(ctypes.byref(h), 4, M, 2.0, 6, 0, None) == 1          # EINVAL: d
+    assert b"d must be" in lib.nfftbl_plan_error()
+    M1 = (ctypes.c_int * 3)(255, 0, 0)
+    assert lib.nfftbl_plan(ctypes.byref(h), 1, M1, 2.0, 6, 0, None) == 1         # odd M
+    assert lib.nfftbl_plan(ctypes.byref(h), 1, M, 2.0, 300, 0, None) == 1        # 2m >= L
+    M3 = (ctypes.c_int * 3)(100, 0, 0)
+    assert lib.nfftbl_plan(ctypes.byref(h), 1, M3, 1.1, 4, 0, None) == 3         # L = 110 not 2^p
+    assert lib.nfftbl_plan(ctypes.byref(h), 1, M, 2.0, 13, 0, None) == 3         # m > 12
+    assert lib.nfftbl_plan(None, 1, M, 2.0, 6, 0, None) == 1
+    assert lib.nfftbl_destroy(None) == 0
+    assert lib.nfftbl_set_nodes(None, 0, None) == 1
+    assert lib.nfftbl_forward(None, None, None) == 1
+    assert lib.nfftbl_last_error(None) == b"NULL plan"

@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Element-by-element comparisons at sizes the oracle finishes in seconds but
+that span several tiles, several work items per tile and ragged tails;
+integer binning results bit for bit.  Tolerances (relative l2 over all
+outputs and batch entries): 1e-12 for FP64 plans, 1e-5 for FP32 plans.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import oracle_plan, rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+nb = pytest.importorskip("paper_2502_07155_gb300")
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32c": 1e-5}
+RDT = {"f64": np.float64, "f32": np.float32, "f32c": np.float32}
+CDT = {"f64": np.complex128, "f32": np.complex64, "f32c": np.complex64}
+
+# (d, M, m, N, nodes_per_item): several tiles, several items per tile, ragged tails
+SHAPES = {
+    1: (256, 8, 1000, 64),
+    2: (64, 6, 3000, 128),
+    3: (32, 4, 3000, 256),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2502_07155_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(d, prec, method="shannon", window="sinh", batch=1, m=None, M=None, N=None, table=None, seed=0,
+         npi=None):
+    M0, m0, N0, npi0 = SHAPES[d]
+    M = M or M0
+    m = m or m0
+    N = N if N is not None else N0
+    plan = nb.Plan(d, M, 2.0, m, window=window, precision=prec, method=method, batch=batch, table=table,
+                   nodes_per_item=npi or npi0)
+    x = W.nodes_uniform(N, d, seed=seed, dtype=RDT[prec])
+    plan.set_nodes(to_dev(x))
+    return plan, x
+
+
+# --------------------------------------------------------------------------- step 0a
+
+@pytest.mark.parametrize("method", ["shannon", "classic"])
+@pytest.mark.parametrize("window", ["sinh", "ckb"])
+def test_precorrection_factors(method, window):
+    plan = nb.Plan(2, (64, 32), 2.0, 5, window=window, method=method, precision="f64")
+    op = oracle_plan(plan)
+    ref = O.precorrection_factors(op)
+    for t in range(2):
+        got = plan.factors(t)
+        assert np.max(np.abs(got - ref[t]) / np.abs(ref[t])) < 1e-13
+
+
+def test_precorrection_factors_table_window():
+    tab = O.learned_table(O.mlp_init())
+    plan = nb.Plan(1, 128, 2.0, 4, window="table", table=tab, precision="f64")
+    op = oracle_plan(plan, table=tab)
+    ref = O.precorrection_factors(op)[0]
+    assert np.max(np.abs(plan.factors(0) - ref) / np.abs(ref)) < 1e-10
+
+
+# --------------------------------------------------------------------------- binning
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_binning_bit_exact(d, prec):
+    plan, x = make(d, prec)
+    # adversarial extras: duplicates, grid points, both edges of the domain
+    L = plan.L[0]
+    extra = np.concatenate([x[:50], np.full((7, d), -0.5), (np.arange(7 * d).reshape(7, d) % L - L // 2) / L,
+                            np.full((3, d), np.nextafter(RDT[prec](0.5), RDT[prec](0)))]).astype(RDT[prec])
+    xs = np.concatenate([x, extra]).astype(RDT[prec])
+    plan.set_nodes(to_dev(xs))
+    keys, perm, off = plan.binning()
+    info = plan.info()
+    rk, rp, roff, ok = O.bin_nodes(xs, plan.L, info["tile"][:d])
+    assert ok
+    np.testing.assert_array_equal(perm.astype(np.int64), rp)
+    np.testing.assert_array_equal(keys.astype(np.int64), rk[rp])
+    np.testing.assert_array_equal(off.astype(np.int64), roff)
+
+
+@pytest.mark.parametrize("bad", [0.5, -0.5000001, np.nan, np.inf])
+def test_binning_domain_error(bad):
+    plan, x = make(2, "f32")
+    x = x.copy()
+    x[17, 1] = bad
+    with pytest.raises(nb.NfftblError) as e:
+        plan.set_nodes(to_dev(x))
+    assert e.value.name == "EDOMAIN"
+    with pytest.raises(nb.NfftblError) as e2:
+        plan.forward(to_dev(W.fhat_gaussian(64, 2, dtype=np.complex64)))
+    assert e2.value.name == "ESTATE"
+
+
+# --------------------------------------------------------------------------- forward / adjoint
+
+CASES = [(d, prec, method) for d in (1, 2, 3) for prec in ("f64", "f32", "f32c") for method in ("shannon", "classic")]
+
+
+@pytest.mark.parametrize("d,prec,method", CASES)
+def test_forward_parity(d, prec, method):
+    batch = 2
+    plan, x = make(d, prec, method=method, batch=batch)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+    f = to_host(plan.forward(to_dev(fh)))
+    plan.sync()
+    op = oracle_plan(plan)
+    ref = O.forward(op, fh, x)
+    assert rel_l2(f, ref) < TOL[prec]
+    # the grid after steps 1-2 (Eq. 4.7)
+    assert rel_l2(plan.grid(), O.grid_samples(op, fh)) < TOL[prec]
+
+
+@pytest.mark.parametrize("d,prec,method", CASES)
+def test_adjoint_parity(d, prec, method):
+    batch = 2
+    plan, x = make(d, prec, method=method, batch=batch)
+    g = W.adjoint_input(x.shape[0], batch=batch, dtype=CDT[prec])
+    fh = to_host(plan.adjoint(to_dev(g)))
+    plan.sync()
+    ref = O.adjoint(oracle_plan(plan), g, x)
+    assert rel_l2(fh, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_adjoint_identity_gpu(d):
+    """<A fhat, g> = <fhat, A^H g> with both sides from the GPU (FP64)."""
+    plan, x = make(d, "f64", batch=1)
+    fh = W.fhat_gaussian(plan.M, dtype=np.complex128)
+    g = W.adjoint_input(x.shape[0], dtype=np.complex128)
+    f = to_host(plan.forward(to_dev(fh)))
+    h = to_host(plan.adjoint(to_dev(g)))
+    lhs = np.vdot(g, f)
+    rhs = np.vdot(h, fh)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("d,prec", [(1, "f64"), (2, "f64"), (3, "f64"), (2, "f32"), (3, "f32")])
+def test_interpolation_property_gpu(d, prec):
+    """Nodes on grid points return the grid values (Section 3, the sinc taps
+    vanish): FP64 to rounding, FP32 to one rounding of phi(0)."""
+    plan, _ = make(d, prec)
+    L = plan.L[0]
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, L, size=(500, d))
+    x = ((idx - L // 2) / L).astype(RDT[prec])
+    plan.set_nodes(to_dev(x))
+    fh = W.fhat_gaussian(plan.M, dtype=CDT[prec])
+    f = to_host(plan.forward(to_dev(fh)))[0]
+    grid = plan.grid()[0]
+    ref = grid[tuple(idx.T)]
+    tol = 1e-15 if prec == "f64" else 3e-7
+    assert np.max(np.abs(f - ref)) <= tol * np.max(np.abs(grid))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_empty_and_single_node(prec):
+    plan, _ = make(2, prec, N=0)
+    fh = W.fhat_gaussian(plan.M, dtype=CDT[prec])
+    f = plan.forward(to_dev(fh))
+    assert f.shape == (1, 0)
+    h = to_host(plan.adjoint(to_dev(np.zeros((1, 0), dtype=CDT[prec]))))
+    assert np.all(h == 0)
+    plan.set_nodes(to_dev(np.array([[0.1234, -0.377]], dtype=RDT[prec])))
+    f1 = to_host(plan.forward(to_dev(fh)))
+    ref = O.forward(oracle_plan(plan), fh, np.array([[0.1234, -0.377]], dtype=RDT[prec]))
+    assert rel_l2(f1, ref) < TOL[prec]
+    plan.sync()
+
+
+@pytest.mark.parametrize("window", ["ckb", "table"])
+def test_other_windows_forward(window):
+    tab = O.learned_table(O.mlp_init()) if window == "table" else None
+    plan = nb.Plan(2, 64, 2.0, 5, window=window, table=tab, precision="f64")
+    x = W.nodes_uniform(2000, 2, dtype=np.float64)
+    plan.set_nodes(to_dev(x))
+    fh = W.fhat_gaussian(64, 2, dtype=np.complex128)
+    f = to_host(plan.forward(to_dev(fh)))
+    ref = O.forward(oracle_plan(plan, table=tab), fh, x)
+    assert rel_l2(f, ref) < (1e-12 if window == "ckb" else 1e-9)
+
+
+# --------------------------------------------------------------------------- node derivative
+
+@pytest.mark.parametrize("d,prec,method", [(1, "f64", "shannon"), (2, "f64", "shannon"), (3, "f64", "shannon"),
+                                           (2, "f64", "classic"), (2, "f32", "shannon"), (3, "f32", "shannon")])
+def test_node_grad_parity(d, prec, method):
+    batch = 2
+    plan, x = make(d, prec, method=method, batch=batch, N=800)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+    gf = W.adjoint_input(x.shape[0], batch=batch, dtype=CDT[prec])
+    gx = to_host(plan.node_grad(to_dev(fh), to_dev(gf)))
+    plan.sync()
+    ref = O.node_grad(oracle_plan(plan), fh, x, gf)
+    assert rel_l2(gx, ref) < (1e-10 if prec == "f64" else 1e-4)
+
+
+# --------------------------------------------------------------------------- launch accounting
+
+def test_kernel_launch_count_grows():
+    plan, _ = make(2, "f32")
+    n0 = plan.kernel_launches()
+    plan.forward(to_dev(W.fhat_gaussian(plan.M, dtype=np.complex64)))
+    plan.sync()
+    assert plan.kernel_launches() == n0 + 3     # two FFT passes + interpolation
