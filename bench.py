@@ -1,0 +1,465 @@
+#!/usr/bin/env python
+"""Throughput of the NFFT-like procedure for bandlimited functions on GB300.
+
+Workload (default, the d = 2 configuration the metric is quoted on): d = 2,
+M = 256 x 256, sigma = 2 (L = 512 x 512), sinh window, m = 8 (the smallest
+m in {4, 6, 8} whose error against the trigonometric sum is <= 1e-6),
+N = 2^20 nodes i.i.d. uniform in [-1/2, 1/2)^2 (float32), fhat complex64
+N(0,1) times the triangle envelope, adjoint input complex64 N(0,1).  All
+inputs are synthetic and seeded (module ``workloads``).
+
+One step = one forward transform (Algorithm 4.2 steps 1-3: precorrection +
+oversampled FFT + short sums) and one adjoint transform (spreading +
+forward-sign FFT + crop/weight) of the FP32 plan on one batch, with the
+nodes already binned (set_nodes is amortised; its time is reported
+separately).  value = N nodes / step time (nodes/s through one
+forward + adjoint round trip).  The L2 cache is flushed (a 256 MiB write)
+before every timed step, outside the timed events.
+
+Also reported: the plain FP64 GPU path on the same inputs and its speed
+ratio, the FP32 error against the FP64 path, per-kernel device times,
+the roofline of the dominant kernel, end-to-end throughput through the
+C-ABI with host buffers, the oracle on the host cores (cpu_baseline) and
+SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "nodes/s at rel. err <=1e-6 (d=2,3): FP32/learned vs plain FP64; % roofline"
+UNIT = "nodes/s"
+
+CONFIGS = {
+    # name: (d, M, m, N, batch, node kind)
+    "d2_M256_m8_N2^20": (2, 256, 8, 1 << 20, 1, "uniform"),
+    "d3_M128_m6_N2^23_spokes": (3, 128, 6, 1 << 23, 1, "spokes"),
+    "d2_M512_m6_N4e6_B8": (2, 512, 6, 4_000_000, 8, "uniform"),
+    "d1_M256_m8_N1024": (1, 256, 8, 1024, 1, "uniform"),
+}
+DEFAULT_CONFIG = "d2_M256_m8_N2^20"
+
+# GB300 unit counts (152 SMs, 128 FP32 lanes and 16 SFU lanes per SM) at the
+# maximum SM clock; the FP32 peak is the ALU roofline of the short-sum kernels.
+SMS = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of this workload: filled from the committed profile summary of the
+# same kernel version, None when not yet captured.
+NCU_TRAFFIC_BYTES = {}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def make_inputs(cfg):
+    d, M, m, N, B, kind = CONFIGS[cfg]
+    if kind == "spokes":
+        x = W.nodes_spokes(n_spokes=1 << 13, per_spoke=N >> 13)
+    else:
+        x = W.nodes_uniform(N, d)
+    envelope = cfg != "d2_M512_m6_N4e6_B8"
+    fh = W.fhat_gaussian(M, d, batch=B, envelope=envelope)
+    g = W.adjoint_input(N, batch=B)
+    return x, fh, g
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        maxm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(maxm) if maxm else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+
+_ORACLE_CHILD = r"""
+import json, sys, time, numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle as O
+z = np.load(sys.argv[2])
+d, M, m = int(z["d"]), int(z["M"]), int(z["m"])
+p = O.make_plan(d, M, 2.0, m, beta=float(z["beta"]))
+fac = O.precorrection_factors(p)
+x, fh, g = z["x"], z["fh"], z["g"]
+t0 = time.perf_counter()
+grid = O.grid_samples(p, fh, fac)
+f = O.step3_short_sums(p, grid, x)
+h = O.adjoint(p, g, x, fac)
+t = time.perf_counter() - t0
+out = {"seconds": t, "n": int(x.shape[0])}
+if "f_gpu" in z.files:
+    fg = z["f_gpu"]
+    out["fp32_vs_oracle_rel_l2"] = float(np.linalg.norm(fg - f) / np.linalg.norm(f))
+    feas = np.flatnonzero(np.all(np.abs(x) < 0.5 - m / (2.0 * M), axis=1))[:2000]
+    if feas.size:
+        nd = O.ndft(fh, x[feas])
+        out["oracle_vs_ndft_rel_l2_feasible"] = float(np.linalg.norm(f[:, feas] - nd) / np.linalg.norm(nd))
+        out["fp32_vs_ndft_rel_l2_feasible"] = float(np.linalg.norm(fg[:, feas] - nd) / np.linalg.norm(nd))
+        out["ndft_sample"] = int(feas.size)
+print(json.dumps(out))
+"""
+
+
+def run_oracle_sample(cfg, x, fh, g, beta, n_sample, f_gpu=None):
+    """Time the oracle (forward + adjoint, single thread) on the first n_sample
+    nodes in a child process (no GPU).  Returns its JSON dict."""
+    d, M, m, N, B, kind = CONFIGS[cfg]
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    arrays = dict(d=d, M=M, m=m, beta=beta, x=x[:n_sample], fh=fh, g=g[:, :n_sample])
+    if f_gpu is not None:
+        arrays["f_gpu"] = f_gpu[:, :n_sample]
+    np.savez(path, **arrays)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        res = subprocess.run([sys.executable, "-c", _ORACLE_CHILD, ROOT, path], capture_output=True, text=True,
+                             env=env, timeout=900)
+    finally:
+        os.unlink(path)
+    if res.returncode != 0:
+        raise RuntimeError("oracle child failed: " + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, cfg):
+    """The oracle as the reference arm: each step is forward + adjoint of the
+    oracle on a bounded sample of the workload's nodes (full grid DFT)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    d, M, m, N, B, kind = CONFIGS[cfg]
+    x, fh, g = make_inputs(cfg)
+    n_sample = min(1 << 13, N)
+    sys.path.insert(0, ROOT)
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = run_oracle_sample(cfg, x, fh, g, float(np.pi * m * 0.5), n_sample)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+    t = float(np.mean(times))
+    value = n_sample / t
+    sample = f"first {n_sample} of the {N} nodes with the full grid DFT (M={M}^{d}, L={2 * M}^{d}), forward + adjoint"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg, "d": d, "M": M, "m": m, "N": N, "batch": B, "nodes": kind},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, cfg):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    if local_rank == 0:
+        from paper_2502_07155_gb300 import build
+        build.build()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist.barrier()
+    import paper_2502_07155_gb300 as nb
+
+    d, M, m, N, B, kind = CONFIGS[cfg]
+    x, fh, g = make_inputs(cfg)
+    dev = torch.device("cuda", local_rank)
+    x_d = torch.from_numpy(x).to(dev)
+    fh_d = torch.from_numpy(fh).to(dev)
+    g_d = torch.from_numpy(g).to(dev)
+
+    plan = nb.Plan(d, M, 2.0, m, precision="f32", batch=B)
+    t0 = time.perf_counter()
+    plan.set_nodes(x_d)
+    t_set_first = time.perf_counter() - t0
+    f_out = torch.empty((B, N), dtype=torch.complex64, device=dev)
+    h_out = torch.empty((B,) + (M,) * d, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(fh_d, out=f_out)
+        plan.adjoint(g_d, out=h_out)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+
+    # set_nodes alone (binning, a1), timed with events (it synchronises)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    set_ms = []
+    for _ in range(3):
+        flush.zero_()
+        ev0.record(stream)
+        plan.set_nodes(x_d)
+        ev1.record(stream)
+        ev1.synchronize()
+        set_ms.append(ev0.elapsed_time(ev1))
+
+    # ---- timed region
+    launches0 = plan.kernel_launches()
+    plan.kernel_timing(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    plan.sync()
+    ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    ktimes = plan.kernel_times()
+    plan.kernel_timing(False)
+    launches = plan.kernel_launches() - launches0
+    t_step = float(np.sum(ms)) / args.steps
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    if args.quick:
+        # timed region only (used for profiling captures): no comparison legs
+        if rank == 0:
+            print(json.dumps({"quick": True, "config": cfg, "ms_per_step": t_step, "value": world * N / (t_step * 1e-3),
+                              "unit": UNIT, "gpu_launches": launches, "clocks": clk,
+                              "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in ktimes.items()}}))
+        if world > 1:
+            dist.destroy_process_group()
+        plan.close()
+        return 0
+
+    # ---- per-direction times (same plan, events around each call)
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return float(np.median(out))
+
+    fwd_ms = timed(lambda: plan.forward(fh_d, out=f_out), max(3, args.steps // 2))
+    adj_ms = timed(lambda: plan.adjoint(g_d, out=h_out), max(3, args.steps // 2))
+    gx = torch.empty((N, d), dtype=torch.float32, device=dev)
+    grad_ms = timed(lambda: plan.node_grad(fh_d, g_d, out=gx), 3)
+    f32 = plan.forward(fh_d, out=f_out).clone()
+    plan.sync()
+
+    # ---- classical NFFT (Algorithm 2.1) on the same inputs, FP32
+    cplan = nb.Plan(d, M, 2.0, m, precision="f32", method="classic", batch=B)
+    cplan.set_nodes(x_d)
+    for _ in range(2):
+        cplan.forward(fh_d, out=f_out)
+        cplan.adjoint(g_d, out=h_out)
+    cls_ms = timed(lambda: (cplan.forward(fh_d, out=f_out), cplan.adjoint(g_d, out=h_out)), 3)
+    cplan.sync()
+    cplan.close()
+
+    # ---- plain FP64 GPU path on the same inputs
+    plan64 = nb.Plan(d, M, 2.0, m, precision="f64", batch=B)
+    x64 = torch.from_numpy(x.astype(np.float64)).to(dev)
+    fh64 = torch.from_numpy(fh.astype(np.complex128)).to(dev)
+    g64 = torch.from_numpy(g.astype(np.complex128)).to(dev)
+    plan64.set_nodes(x64)
+    f64o = torch.empty((B, N), dtype=torch.complex128, device=dev)
+    h64o = torch.empty((B,) + (M,) * d, dtype=torch.complex128, device=dev)
+    plan64.forward(fh64, out=f64o)
+    plan64.adjoint(g64, out=h64o)
+    plan64.sync()
+    reps64 = 2 if N * (2 * m) ** d > 5e9 else 3
+    f64_ms = timed(lambda: (plan64.forward(fh64, out=f64o), plan64.adjoint(g64, out=h64o)), reps64)
+    f64 = plan64.forward(fh64, out=f64o)
+    plan64.sync()
+    err_fp32_fp64 = float(torch.linalg.vector_norm(f32.to(torch.complex128) - f64) / torch.linalg.vector_norm(f64))
+    plan64.close()
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    fh_h = torch.from_numpy(fh).pin_memory()
+    g_h = torch.from_numpy(g).pin_memory()
+    f_h = torch.empty((B, N), dtype=torch.complex64).pin_memory()
+    h_h = torch.empty((B,) + (M,) * d, dtype=torch.complex64).pin_memory()
+
+    def e2e_step():
+        fh_d.copy_(fh_h, non_blocking=True)
+        g_d.copy_(g_h, non_blocking=True)
+        plan.forward(fh_d, out=f_out)
+        f_h.copy_(f_out, non_blocking=True)
+        plan.adjoint(g_d, out=h_out)
+        h_h.copy_(h_out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_t = float(np.mean(e2e_ms))
+    h2d = fh_h.numel() * 8 + g_h.numel() * 8
+    d2h = f_h.numel() * 8 + h_h.numel() * 8
+
+    # ---- roofline of the dominant short-sum kernel
+    dom = max(("interp", "spread"), key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    per_launch_s = dom_ms / max(dom_n, 1) * 1e-3
+    flops = 5.0 * (2 * m) ** d * N * B            # algorithmic FP32 flops per launch
+    achieved = flops / per_launch_s / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = NCU_TRAFFIC_BYTES.get((cfg, dom))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "flops_per_launch": flops,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+
+    result = None
+    if rank == 0:
+        # cpu baseline: the oracle on a bounded sample of the same workload
+        n_sample = 1 << 18 if d <= 2 else 1 << 13
+        n_sample = min(n_sample, N)
+        cb = run_oracle_sample(cfg, x, fh, g, plan.beta, n_sample, f_gpu=f32.cpu().numpy())
+        cpu_value = cb["n"] / cb["seconds"]
+        value = world * N / (t_step * 1e-3)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg, "d": d, "M": M, "sigma": 2.0, "L": 2 * M, "m": m, "N": N, "batch": B,
+                       "nodes": kind, "window": "sinh", "beta": plan.beta,
+                       "step": "forward + adjoint (nodes binned once)", "l2": "flushed (256 MiB write) before each step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "e2e": {"value": world * N / (e2e_t * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {cb['n']} of the {N} nodes, full grid DFT, forward + adjoint, "
+                                       f"one thread ({cb['seconds']:.1f} s)"},
+            "clocks": clk,
+            "breakdown_ms": {"forward": fwd_ms, "adjoint": adj_ms, "set_nodes": float(np.median(set_ms)),
+                             "set_nodes_first_call_s": t_set_first, "node_grad": grad_ms,
+                             "kernels_in_timed_region": {k: {"ms_total": v[0], "launches": v[1]}
+                                                         for k, v in ktimes.items()}},
+            "fp64": {"ms_per_step": f64_ms, "nodes_per_s": N / (f64_ms * 1e-3), "speedup_fp32": f64_ms / t_step},
+            "classic_nfft_fp32": {"ms_per_step": cls_ms, "nodes_per_s": N / (cls_ms * 1e-3)},
+            "accuracy": {"fp32_vs_fp64_gpu_rel_l2": err_fp32_fp64,
+                         **{k: v for k, v in cb.items() if k not in ("seconds", "n")}},
+        }
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT_CONFIG)
+    ap.add_argument("--quick", action="store_true",
+                    help="timed region only (no FP64, classical, end-to-end or oracle legs); for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args, args.config)
+    return run_ours(args, args.config)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

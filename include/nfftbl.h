@@ -227,6 +227,27 @@ nfftbl_status nfftbl_spread_grid(nfftbl_plan_t plan, const void* f_dev);
 /* Number of this library's kernels launched on the plan so far (all calls). */
 int64_t nfftbl_kernel_launches(nfftbl_plan_t plan);
 
+/* Kernel classes for the per-kernel timers below. */
+typedef enum {
+    NFFTBL_K_FFT = 0,       /* FFT passes (steps 1-2 and their adjoint)     */
+    NFFTBL_K_INTERP = 1,    /* short sums, step 3                           */
+    NFFTBL_K_SPREAD = 2,    /* transposed short sums                        */
+    NFFTBL_K_GRAD = 3,      /* node derivative                              */
+    NFFTBL_K_BIN = 4,       /* binning (keys, sort, offsets)                */
+    NFFTBL_K_COUNT = 5
+} nfftbl_kernel_class;
+
+/* enable != 0: record a CUDA event pair on the plan's stream around every
+ * later kernel launch of this plan (adds two event records per launch);
+ * enable == 0: stop recording.  Either way the accumulated times are reset. */
+nfftbl_status nfftbl_kernel_timing(nfftbl_plan_t plan, int enable);
+
+/* Synchronise the recorded events and return, per kernel class, the summed
+ * device time in milliseconds (ms_out) and the number of launches
+ * (count_out), each an array of NFFTBL_K_COUNT entries (host memory).  The
+ * accumulators are reset afterwards. */
+nfftbl_status nfftbl_kernel_times(nfftbl_plan_t plan, double* ms_out, int64_t* count_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,9 @@ EXPORTED = [
     "nfftbl_adjoint", "nfftbl_node_grad", "nfftbl_sync", "nfftbl_destroy", "nfftbl_last_error",
     "nfftbl_plan_error", "nfftbl_get_info", "nfftbl_get_factors", "nfftbl_get_binning", "nfftbl_get_grid",
     "nfftbl_grid_ptr", "nfftbl_interp_grid", "nfftbl_spread_grid", "nfftbl_kernel_launches",
+    "nfftbl_kernel_timing", "nfftbl_kernel_times",
 ]
+KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin")
 
 
 class NfftblError(RuntimeError):
@@ -110,6 +112,10 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_spread_grid.restype = st
     L.nfftbl_kernel_launches.argtypes = [P]
     L.nfftbl_kernel_launches.restype = ctypes.c_int64
+    L.nfftbl_kernel_timing.argtypes = [P, ctypes.c_int]
+    L.nfftbl_kernel_timing.restype = st
+    L.nfftbl_kernel_times.argtypes = [P, P, P]
+    L.nfftbl_kernel_times.restype = st
     _lib = L
     return L
 
@@ -317,6 +323,18 @@ class Plan:
 
     def kernel_launches(self) -> int:
         return int(self._lib.nfftbl_kernel_launches(self._h))
+
+    def kernel_timing(self, enable: bool = True):
+        """Record CUDA events around each later kernel launch (resets sums)."""
+        self._check(self._lib.nfftbl_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        """{class: (total_ms, launches)} since the last call; resets."""
+        ms = np.zeros(5, dtype=np.float64)
+        cnt = np.zeros(5, dtype=np.int64)
+        self._check(self._lib.nfftbl_kernel_times(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                                  cnt.ctypes.data_as(ctypes.c_void_p)))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

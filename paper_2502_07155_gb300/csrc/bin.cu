@@ -225,6 +225,7 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     uint32_t* vA = static_cast<uint32_t*>(p->perm.p);
     uint32_t* kB = static_cast<uint32_t*>(p->keys_tmp.p);
     uint32_t* vB = static_cast<uint32_t*>(p->perm_tmp.p);
+    timing_begin(p, NFFTBL_K_BIN);   // one timed span for the whole binning sequence
     if (N > 0) {
         if (dbl)
             key_kernel<double><<<grid1d(N, 256), 256, 0, s>>>(static_cast<const double*>(x_dev), N, p->geom, kA,
@@ -269,6 +270,7 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     emit_work_kernel<<<grid1d(p->n_tiles, 256), 256, 0, s>>>(off, chunk_start, p->n_tiles, K,
                                                              static_cast<WorkItem*>(p->work.p));
     p->launches += 4;
+    timing_end(p);
     if ((st = check_cuda(p, cudaGetLastError(), "binning launch")) != NFFTBL_OK) return st;
     uint32_t host_total = 0;
     if ((st = check_cuda(p, cudaMemcpyAsync(&host_total, counters, 4, cudaMemcpyDeviceToHost, s), "read work total")) !=

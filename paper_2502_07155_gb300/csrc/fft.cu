@@ -204,9 +204,11 @@ nfftbl_status run_pass(nfftbl_plan_s* p, const void* in, void* out, int t) {
                                   "fft smem attribute");
     if (st != NFFTBL_OK) return st;
     long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
+    timing_begin(p, NFFTBL_K_FFT);
     kern<<<static_cast<unsigned>(blocks), kFftThreads, smem, p->stream>>>(
         static_cast<const C2<T>*>(in), static_cast<C2<T>*>(out), outer, static_cast<int>(inner), M, L, W,
         static_cast<const T*>(p->facT[t].p), static_cast<const C2<T>*>(p->tw[t].p));
+    timing_end(p);
     p->launches++;
     return check_cuda(p, cudaGetLastError(), "fft pass launch");
 }

@@ -183,6 +183,11 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->counters);
     free_buf(p->err);
     if (p->err_host) cudaFreeHost(p->err_host);
+    for (auto& t : p->timed) {
+        if (t.a) cudaEventDestroy(t.a);
+        if (t.b) cudaEventDestroy(t.b);
+    }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
     delete p;
 }
 
@@ -199,6 +204,34 @@ nfftbl_status plan_fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& m
 nfftbl_status fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& msg) {
     if (p) p->last_error = msg;
     return st;
+}
+
+namespace {
+cudaEvent_t take_event(nfftbl_plan_s* p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+}  // namespace
+
+void timing_begin(nfftbl_plan_s* p, int kind) {
+    if (!p->timing) return;
+    nfftbl_plan_s::Timed t{kind, take_event(p), take_event(p)};
+    if (t.a) cudaEventRecord(t.a, p->stream);
+    p->timed.push_back(t);
+}
+
+void timing_end(nfftbl_plan_s* p) {
+    if (!p->timing || p->timed.empty()) return;
+    if (p->timed.back().b) cudaEventRecord(p->timed.back().b, p->stream);
 }
 
 nfftbl_status check_cuda(nfftbl_plan_s* p, cudaError_t e, const char* what) {
@@ -561,5 +594,38 @@ nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t p, void** grid_dev) {
 }
 
 int64_t nfftbl_kernel_launches(nfftbl_plan_t p) { return p ? p->launches : 0; }
+
+nfftbl_status nfftbl_kernel_timing(nfftbl_plan_t p, int enable) {
+    if (!p) return NFFTBL_EINVAL;
+    double ms[NFFTBL_K_COUNT];
+    int64_t cnt[NFFTBL_K_COUNT];
+    nfftbl_status st = nfftbl_kernel_times(p, ms, cnt);   // drain and reset
+    p->timing = enable != 0;
+    return st;
+}
+
+nfftbl_status nfftbl_kernel_times(nfftbl_plan_t p, double* ms_out, int64_t* count_out) {
+    if (!p || !ms_out || !count_out) return NFFTBL_EINVAL;
+    for (int k = 0; k < NFFTBL_K_COUNT; ++k) {
+        ms_out[k] = 0.0;
+        count_out[k] = 0;
+    }
+    nfftbl_status st = NFFTBL_OK;
+    for (auto& t : p->timed) {
+        if (t.a && t.b && st == NFFTBL_OK) {
+            float ms = 0.f;
+            st = check_cuda(p, cudaEventSynchronize(t.b), "timing event sync");
+            if (st == NFFTBL_OK) st = check_cuda(p, cudaEventElapsedTime(&ms, t.a, t.b), "timing elapsed");
+            if (st == NFFTBL_OK && t.kind >= 0 && t.kind < NFFTBL_K_COUNT) {
+                ms_out[t.kind] += ms;
+                count_out[t.kind] += 1;
+            }
+        }
+        if (t.a) p->event_pool.push_back(t.a);
+        if (t.b) p->event_pool.push_back(t.b);
+    }
+    p->timed.clear();
+    return st;
+}
 
 }  // extern "C"

@@ -113,9 +113,22 @@ struct nfftbl_plan_s {
 
     nfftbl::DeviceBuf err;                // device error word
     int* err_host = nullptr;              // pinned mirror
+
+    // optional per-kernel timing (nfftbl_kernel_timing)
+    bool timing = false;
+    struct Timed {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace nfftbl {
+
+// Per-kernel timing hooks (plan.cu): bracket one launch on the plan's stream.
+void timing_begin(nfftbl_plan_s* p, int kind);
+void timing_end(nfftbl_plan_s* p);
 
 // Allocation helpers (plan.cu).
 nfftbl_status ensure_buf(nfftbl_plan_s* p, DeviceBuf& b, size_t bytes);

@@ -676,12 +676,14 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     const long long want = static_cast<long long>(occ) * p->num_sms;
     const unsigned grid = static_cast<unsigned>(std::max<long long>(1, std::min<long long>(want, args.n_work)));
     if (args.n_work == 0) return NFFTBL_OK;
+    timing_begin(p, kind == TAP_INTERP ? NFFTBL_K_INTERP : kind == TAP_SPREAD ? NFFTBL_K_SPREAD : NFFTBL_K_GRAD);
     if (kind == TAP_INTERP)
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
     else if (kind == TAP_SPREAD)
         spread_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(args);
     else
         node_grad_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
+    timing_end(p);
     p->launches++;
     return check_cuda(p, cudaGetLastError(), "tap kernel launch");
 }
