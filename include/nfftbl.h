@@ -177,8 +177,8 @@ nfftbl_status nfftbl_destroy(nfftbl_plan_t plan);
  * plan).  Valid until the next call on the plan. */
 const char* nfftbl_last_error(nfftbl_plan_t plan);
 
-/* Text of the last nfftbl_plan failure in this thread (the plan handle is NULL
- * then). */
+/* Text of the last failure in this thread of a call that has no plan to hold
+ * it: nfftbl_plan (the plan handle is NULL then) and nfftbl_grid_noalloc. */
 const char* nfftbl_plan_error(void);
 
 /* ---------------------------------------------------------------------------
@@ -247,6 +247,44 @@ nfftbl_status nfftbl_kernel_timing(nfftbl_plan_t plan, int enable);
  * (count_out), each an array of NFFTBL_K_COUNT entries (host memory).  The
  * accumulators are reset afterwards. */
 nfftbl_status nfftbl_kernel_times(nfftbl_plan_t plan, double* ms_out, int64_t* count_out);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free equispaced samples.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code running under another framework's memory
+ * pool or allocator hooks, code that must not allocate while a CUDA graph is
+ * being captured, or hosts that only hand out buffers they allocated
+ * themselves.  nfftbl_plan allocates (window factors, grid, scratch), so such
+ * callers cannot use a plan; this call needs none.
+ *
+ * It computes what nfftbl_forward computes before its short sums: the
+ * precorrected, zero-padded, oversampled inverse FFT of fhat (steps 1-2,
+ * vartheta of Eq. 4.7) for the Shannon method with the sinh window, in FP32:
+ *   d, M, sigma, m, beta, batch : as for nfftbl_plan (beta <= 0: default
+ *                                 pi m (1 - 1/sigma)); batch B >= 1;
+ *   fhat_dev  : B x prod(M_t) complex64 input (centred, row-major), caller-owned;
+ *   grid_dev  : B x prod(L_t) complex64 output (centred, row-major), caller-owned;
+ *   cuda_stream : cudaStream_t the work is enqueued on (NULL = legacy stream).
+ * The result equals the grid a plan with the same parameters holds after
+ * nfftbl_forward.
+ *
+ * It allocates nothing: the window factors, twiddles and intermediate FFT
+ * passes live in one fixed device array of 16 MiB inside the library, which
+ * every GPU that loads the library holds until the process exits.  Problems
+ * whose factors, twiddles and intermediates need more than 16 MiB
+ * (d = 2: about B * M_0 * L_1 * 8 bytes; d = 3: B * M_0 * L_2 * (M_1 + L_1) * 8
+ * bytes) are rejected with NFFTBL_EINVAL and a message naming the size.
+ * The first call on a device looks up that device's address of the array
+ * (with the device current); make the first call on each device before any
+ * stream capture.  Every call shares the one array and leaves its contents
+ * behind: calls whose work overlaps on the GPU (different streams, or
+ * different threads without ordering) race on it, so serialise them.
+ * Asynchronous; errors: EINVAL, EUNSUPPORTED (as for nfftbl_plan), ECUDA.
+ * The message of a failed call is available from nfftbl_plan_error().
+ */
+nfftbl_status nfftbl_grid_noalloc(int d, const int* M, double sigma, int m, double beta, int batch,
+                                  const void* fhat_dev, void* grid_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

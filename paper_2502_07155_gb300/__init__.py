@@ -35,7 +35,7 @@ EXPORTED = [
     "nfftbl_adjoint", "nfftbl_node_grad", "nfftbl_sync", "nfftbl_destroy", "nfftbl_last_error",
     "nfftbl_plan_error", "nfftbl_get_info", "nfftbl_get_factors", "nfftbl_get_binning", "nfftbl_get_grid",
     "nfftbl_grid_ptr", "nfftbl_interp_grid", "nfftbl_spread_grid", "nfftbl_kernel_launches",
-    "nfftbl_kernel_timing", "nfftbl_kernel_times",
+    "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
 ]
 KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin")
 
@@ -116,6 +116,9 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_kernel_timing.restype = st
     L.nfftbl_kernel_times.argtypes = [P, P, P]
     L.nfftbl_kernel_times.restype = st
+    L.nfftbl_grid_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, P, P, P]
+    L.nfftbl_grid_noalloc.restype = st
     _lib = L
     return L
 
@@ -346,6 +349,32 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def grid_noalloc(fhat, sigma: float, m: int, grid=None, beta: float | None = None):
+    """Steps 1-2 without any device allocation inside the library
+    (C-ABI nfftbl_grid_noalloc): fhat (B, M_0, .., M_{d-1}) complex64 CUDA
+    tensor -> grid (B, L_0, .., L_{d-1}) complex64.  For callers that cannot
+    allocate device memory through the library; pass ``grid`` to supply the
+    output buffer as well.  Calls that overlap on the GPU share one fixed
+    scratch array and must be serialised."""
+    torch = _torch()
+    L_ = lib()
+    d = fhat.dim() - 1
+    Ms = [int(v) for v in fhat.shape[1:]]
+    Ls = [oversampled_length(v, sigma) for v in Ms]
+    if fhat.dtype != torch.complex64 or not fhat.is_cuda or not fhat.is_contiguous():
+        raise TypeError("fhat must be a contiguous complex64 CUDA tensor")
+    if grid is None:
+        grid = torch.empty([fhat.shape[0]] + Ls, dtype=torch.complex64, device=fhat.device)
+    Marr = (ctypes.c_int * 3)(*(Ms + [0] * (3 - d)))
+    st = L_.nfftbl_grid_noalloc(d, Marr, float(sigma), int(m), 0.0 if beta is None else float(beta),
+                                int(fhat.shape[0]), ctypes.c_void_p(fhat.data_ptr()),
+                                ctypes.c_void_p(grid.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise NfftblError(st, L_.nfftbl_plan_error().decode())
+    return grid
 
 
 class _DevicePtr:

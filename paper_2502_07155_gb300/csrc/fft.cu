@@ -242,6 +242,23 @@ nfftbl_status adjoint_impl(nfftbl_plan_s* p, void* fhat) {
 
 }  // namespace
 
+// One forward pass along dimension t of an array whose dimensions before t
+// keep their M extent and whose dimensions after t already have their L
+// extent (outer / inner line counts), for callers that own every buffer.
+cudaError_t launch_fft_forward_pass_f32(const void* in, void* out, long long outer, long long inner, int M, int L,
+                                        const float* fac, const void* tw, cudaStream_t s) {
+    const int W = choose_lines<float>(L, inner);
+    const size_t smem = fft_smem<float>(L, W);
+    auto kern = fft_pass_kernel<float, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
+    kern<<<static_cast<unsigned>(blocks), kFftThreads, smem, s>>>(
+        static_cast<const float2*>(in), static_cast<float2*>(out), outer, static_cast<int>(inner), M, L, W, fac,
+        static_cast<const float2*>(tw));
+    return cudaGetLastError();
+}
+
 // Scratch layout: d = 2 uses tmpA (B M0 L1); d = 3 uses tmpA (B M0 M1 L2)
 // and tmpB (B M0 L1 L2).
 nfftbl_status fft_forward(nfftbl_plan_s* p, const void* fhat) {

@@ -206,6 +206,8 @@ nfftbl_status fail(nfftbl_plan_s* p, nfftbl_status st, const std::string& msg) {
     return st;
 }
 
+void set_plan_error(const std::string& msg) { g_plan_error = msg; }
+
 namespace {
 cudaEvent_t take_event(nfftbl_plan_s* p) {
     if (!p->event_pool.empty()) {

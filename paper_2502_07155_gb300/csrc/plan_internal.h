@@ -130,6 +130,9 @@ namespace nfftbl {
 void timing_begin(nfftbl_plan_s* p, int kind);
 void timing_end(nfftbl_plan_s* p);
 
+// Message returned by nfftbl_plan_error() for calls without a plan (plan.cu).
+void set_plan_error(const std::string& msg);
+
 // Allocation helpers (plan.cu).
 nfftbl_status ensure_buf(nfftbl_plan_s* p, DeviceBuf& b, size_t bytes);
 void free_buf(DeviceBuf& b);
@@ -150,6 +153,8 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev);
 // fft.cu
 nfftbl_status fft_forward(nfftbl_plan_s* p, const void* fhat);
 nfftbl_status fft_adjoint(nfftbl_plan_s* p, void* fhat);
+cudaError_t launch_fft_forward_pass_f32(const void* in, void* out, long long outer, long long inner, int M, int L,
+                                        const float* fac, const void* tw, cudaStream_t s);
 
 // Short-sum kernels (taps.cuh).  launch_tap_kernel is instantiated once per
 // (precision, dimension, tap count W = 2m, or W = 0 for m read at run time)
