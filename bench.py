@@ -51,6 +51,8 @@ CONFIGS = {
     "d3_M128_m6_N2^23_spokes": (3, 128, 6, 1 << 23, 1, "spokes"),
     "d2_M512_m6_N4e6_B8": (2, 512, 6, 4_000_000, 8, "uniform"),
     "d1_M256_m8_N1024": (1, 256, 8, 1024, 1, "uniform"),
+    # smaller spoke case for profiler captures (same density profile, 1/8 of the nodes)
+    "d3_M128_m6_N2^20_spokes": (3, 128, 6, 1 << 20, 1, "spokes"),
 }
 DEFAULT_CONFIG = "d2_M256_m8_N2^20"
 

@@ -234,7 +234,8 @@ typedef enum {
     NFFTBL_K_SPREAD = 2,    /* transposed short sums                        */
     NFFTBL_K_GRAD = 3,      /* node derivative                              */
     NFFTBL_K_BIN = 4,       /* binning (keys, sort, offsets)                */
-    NFFTBL_K_COUNT = 5
+    NFFTBL_K_FLUSH = 5,     /* ordered flush of the spread boxes to the grid */
+    NFFTBL_K_COUNT = 6
 } nfftbl_kernel_class;
 
 /* enable != 0: record a CUDA event pair on the plan's stream around every

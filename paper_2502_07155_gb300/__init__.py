@@ -37,7 +37,7 @@ EXPORTED = [
     "nfftbl_grid_ptr", "nfftbl_interp_grid", "nfftbl_spread_grid", "nfftbl_kernel_launches",
     "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
 ]
-KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin")
+KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin", "flush")
 
 
 class NfftblError(RuntimeError):
@@ -333,8 +333,8 @@ class Plan:
 
     def kernel_times(self) -> dict:
         """{class: (total_ms, launches)} since the last call; resets."""
-        ms = np.zeros(5, dtype=np.float64)
-        cnt = np.zeros(5, dtype=np.int64)
+        ms = np.zeros(len(KERNEL_CLASSES), dtype=np.float64)
+        cnt = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
         self._check(self._lib.nfftbl_kernel_times(self._h, ms.ctypes.data_as(ctypes.c_void_p),
                                                   cnt.ctypes.data_as(ctypes.c_void_p)))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}

@@ -212,8 +212,9 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     const long long nblocks = std::max<long long>(1, (N + kRsSeg - 1) / kRsSeg);
     if ((st = ensure_buf(p, p->hist, 256 * nblocks * 4)) != NFFTBL_OK) return st;
     if ((st = ensure_buf(p, p->tile_off, (p->n_tiles + 1) * 4)) != NFFTBL_OK) return st;
-    // counters: [0] work total; chunk starts follow in a separate region
-    if ((st = ensure_buf(p, p->counters, (p->n_tiles + 8) * 4)) != NFFTBL_OK) return st;
+    // counters: [0] scan total of the radix sort; tile_items: first work item per tile
+    if ((st = ensure_buf(p, p->counters, 16)) != NFFTBL_OK) return st;
+    if ((st = ensure_buf(p, p->tile_items, (p->n_tiles + 1) * 4)) != NFFTBL_OK) return st;
     const long long max_work = (N + K - 1) / K + p->n_tiles + 1;
     if ((st = ensure_buf(p, p->work, max_work * sizeof(WorkItem))) != NFFTBL_OK) return st;
 
@@ -263,17 +264,17 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     }
     uint32_t* off = static_cast<uint32_t*>(p->tile_off.p);
     tile_bounds_kernel<<<grid1d(N + 1, 256), 256, 0, s>>>(kA, N, p->geom.cells_per_tile_log2, p->n_tiles, off);
-    uint32_t* counters = static_cast<uint32_t*>(p->counters.p);
-    uint32_t* chunk_start = counters + 4;
+    uint32_t* chunk_start = static_cast<uint32_t*>(p->tile_items.p);
+    uint32_t* work_total = chunk_start + p->n_tiles;
     chunk_count_kernel<<<grid1d(p->n_tiles, 256), 256, 0, s>>>(off, p->n_tiles, K, chunk_start);
-    scan_exclusive_kernel<<<1, kScanThreads, 0, s>>>(chunk_start, p->n_tiles, counters);
+    scan_exclusive_kernel<<<1, kScanThreads, 0, s>>>(chunk_start, p->n_tiles, work_total);
     emit_work_kernel<<<grid1d(p->n_tiles, 256), 256, 0, s>>>(off, chunk_start, p->n_tiles, K,
                                                              static_cast<WorkItem*>(p->work.p));
     p->launches += 4;
     timing_end(p);
     if ((st = check_cuda(p, cudaGetLastError(), "binning launch")) != NFFTBL_OK) return st;
     uint32_t host_total = 0;
-    if ((st = check_cuda(p, cudaMemcpyAsync(&host_total, counters, 4, cudaMemcpyDeviceToHost, s), "read work total")) !=
+    if ((st = check_cuda(p, cudaMemcpyAsync(&host_total, work_total, 4, cudaMemcpyDeviceToHost, s), "read work total")) !=
         NFFTBL_OK)
         return st;
     if ((st = check_cuda(p, cudaMemcpyAsync(p->err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s), "read err")) !=
@@ -286,6 +287,15 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
         return fail(p, NFFTBL_EDOMAIN, "a node coordinate is outside [-1/2, 1/2) or NaN");
     }
     if (host_total > static_cast<uint32_t>(max_work)) return fail(p, NFFTBL_EINTERNAL, "work list overflow");
+    // scratch for the spread boxes: one slot per (work item, batch entry)
+    long long cells = 1;
+    for (int t = 0; t < d; ++t) cells *= p->geom.box[t];
+    const size_t cb = dbl ? 16 : 8;
+    if ((st = ensure_buf(p, p->part, static_cast<size_t>(std::max<uint32_t>(host_total, 1)) * p->batch * cells * cb)) !=
+        NFFTBL_OK) {
+        p->N = -1;
+        return st;
+    }
     p->n_work = host_total;
     p->N = N;
     return NFFTBL_OK;

@@ -136,7 +136,39 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
     a.grid = static_cast<C2<T>*>(p->grid.p);
     a.grid_stride = prod_L(p);
     a.err = static_cast<int*>(p->err.p);
+    a.part = static_cast<C2<T>*>(p->part.p);
+    a.tile_items = static_cast<const uint32_t*>(p->tile_items.p);
+    a.wbound = T(1);
+    if (p->window == NFFTBL_WIN_TABLE) {
+        double mx = 1.0;
+        for (double v : p->table_host) mx = std::max(mx, std::fabs(v));
+        a.wbound = static_cast<T>(std::pow(mx, p->d));
+    }
     return a;
+}
+
+// Batch entries per box group and nodes per pass of the spread kernel: the
+// smallest configuration must fit the device's shared memory; grow the batch
+// group while the block stays within about half an SM's shared memory.
+template <typename T>
+bool spread_config(const nfftbl_plan_s* p, int& nb, int& sub, size_t& bytes) {
+    const int A = tap_array_len(p->m);
+    const int cells = static_cast<int>(box_cells(p->geom));
+    const size_t limit = static_cast<size_t>(p->smem_optin);
+    auto layout = [&](int nbv, int subv) { return spread_smem_layout<T>(p->d, A, cells, nbv, subv).total; };
+    for (sub = 256; sub >= 32; sub /= 2) {
+        bytes = layout(1, sub);
+        if (bytes <= limit) break;
+    }
+    if (bytes > limit) return false;
+    nb = 1;
+    while (nb < p->batch) {
+        const size_t nbytes = layout(nb + 1, sub);
+        if (nbytes > std::min<size_t>(limit, 110 * 1024)) break;
+        ++nb;
+        bytes = nbytes;
+    }
+    return true;
 }
 
 template <typename T>
@@ -147,7 +179,14 @@ nfftbl_status run_taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, 
     a.gradx = static_cast<T*>(gradx);
     // box slots padded to 128 bytes, plus 128 bytes to align the base
     const size_t slot = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
-    const size_t smem = static_cast<size_t>(a.batch_smem) * slot + 128;
+    size_t smem = static_cast<size_t>(a.batch_smem) * slot + 128;
+    if (kind == TAP_SPREAD) {
+        int nb = 1, sub = 32;
+        if (!spread_config<T>(p, nb, sub, smem))
+            return fail(p, NFFTBL_EUNSUPPORTED, "spread box does not fit in shared memory");
+        a.spread_batch = nb;
+        a.spread_sub = sub;
+    }
     switch (p->d) {
         case 1: return run_taps_d<T, 1>(p, a, kind, smem);
         case 2: return run_taps_d<T, 2>(p, a, kind, smem);
@@ -180,6 +219,8 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->hist);
     free_buf(p->tile_off);
     free_buf(p->work);
+    free_buf(p->tile_items);
+    free_buf(p->part);
     free_buf(p->counters);
     free_buf(p->err);
     if (p->err_host) cudaFreeHost(p->err_host);
@@ -331,11 +372,21 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     }
     const size_t cb = (o.precision == NFFTBL_F64) ? 16 : 8;
     TileGeom g{};
+    int dev_for_limits = 0, optin = 0;
+    if (cudaGetDevice(&dev_for_limits) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_for_limits) != cudaSuccess) {
+        cudaGetLastError();
+        return plan_fail(nullptr, NFFTBL_ECUDA, "cannot query the device");
+    }
     while (true) {
         set_geom(g, d, L, T, m);
         const size_t bytes = static_cast<size_t>(box_cells(g)) * cb;
         const bool tma_ok = 2 * g.box[d - 1] <= 256 && (d < 2 || g.box[0] <= 256) && (d < 3 || g.box[1] <= 256);
-        if (bytes <= kBoxMax && tma_ok) break;
+        const int bc = static_cast<int>(box_cells(g));
+        const int A = tap_array_len(m);
+        const size_t spread_min = (o.precision == NFFTBL_F64) ? spread_smem_layout<double>(d, A, bc, 1, 32).total
+                                                              : spread_smem_layout<float>(d, A, bc, 1, 32).total;
+        if (bytes <= kBoxMax && tma_ok && spread_min <= static_cast<size_t>(optin)) break;
         if (user_tile) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "tile box exceeds shared memory or TMA limits");
         int big = 0;
         for (int t = 1; t < d; ++t)
@@ -360,6 +411,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     p->batch = o.batch;
     p->nodes_per_item = o.nodes_per_item > 0 ? o.nodes_per_item : 1024;
     p->geom = g;
+    p->smem_optin = optin;
     p->key_bits = key_bits;
     p->n_tiles = 1;
     for (int t = 0; t < d; ++t) p->n_tiles *= g.nt[t];
@@ -470,8 +522,7 @@ nfftbl_status nfftbl_adjoint(nfftbl_plan_t p, const void* f_dev, void* fhat_dev)
     nfftbl_status st = ready(p);
     if (st != NFFTBL_OK) return st;
     if (!fhat_dev || (!f_dev && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
-    const size_t bytes = static_cast<size_t>(p->batch) * prod_L(p) * complex_bytes(p);
-    if ((st = check_cuda(p, cudaMemsetAsync(p->grid.p, 0, bytes, p->stream), "grid clear")) != NFFTBL_OK) return st;
+    // the ordered flush writes every grid cell: no clearing needed
     if ((st = taps(p, TAP_SPREAD, f_dev, nullptr, nullptr)) != NFFTBL_OK) return st;
     return fft_adjoint(p, fhat_dev);
 }
@@ -495,8 +546,6 @@ nfftbl_status nfftbl_spread_grid(nfftbl_plan_t p, const void* f_dev) {
     nfftbl_status st = ready(p);
     if (st != NFFTBL_OK) return st;
     if (!f_dev && p->N > 0) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
-    const size_t bytes = static_cast<size_t>(p->batch) * prod_L(p) * complex_bytes(p);
-    if ((st = check_cuda(p, cudaMemsetAsync(p->grid.p, 0, bytes, p->stream), "grid clear")) != NFFTBL_OK) return st;
     return taps(p, TAP_SPREAD, f_dev, nullptr, nullptr);
 }
 

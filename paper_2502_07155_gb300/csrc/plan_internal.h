@@ -56,7 +56,43 @@ struct TapArgs {
     C2<T>* fout;               // B x N (interp output)
     T* gradx;                  // N x d (node gradient output)
     int* err;
+    // spreading
+    C2<T>* part;               // n_work x B x box cells: per-item boxes (ordered flush)
+    const uint32_t* tile_items;// n_tiles + 1: first work item of each tile
+    int spread_sub;            // nodes staged per pass in shared memory
+    int spread_batch;          // batch entries per shared-memory box group
+    T wbound;                  // bound on prod_t |window factor| (1 for sinh / cKB)
 };
+
+// Shared-memory layout of spread_kernel (byte offsets), shared with the host.
+struct SpreadSmem {
+    size_t box, lb, w, g, run, red, total;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ SpreadSmem spread_smem_layout(int d, int A, int box_cells, int nb, int sub) {
+    auto al = [](size_t v) { return (v + 15) / 16 * 16; };
+    SpreadSmem L{};
+    const size_t slot = static_cast<size_t>((box_cells + 1) / 2 * 2);   // u64 pairs, even count
+    L.box = 0;
+    L.lb = al(L.box + static_cast<size_t>(nb) * slot * 16);
+    L.w = al(L.lb + static_cast<size_t>(sub) * 4);
+    L.g = al(L.w + static_cast<size_t>(sub) * d * A * sizeof(T));
+    L.run = al(L.g + static_cast<size_t>(nb) * sub * 2 * sizeof(T));
+    L.red = al(L.run + static_cast<size_t>(sub + 1) * 4);
+    L.total = al(L.red + 34 * 8);
+    return L;
+}
+
+// Length of the per-dimension tap arrays of the short-sum kernels: 2m for
+// the compile-time truncations (NFFTBL_FIXED_M_LIST), 24 for the kernel that
+// takes m at run time.
+inline int tap_array_len(int m) {
+    switch (m) {
+        case 2: case 3: case 4: case 5: case 6: case 8: return 2 * m;
+        default: return 24;
+    }
+}
 
 struct DeviceBuf {
     void* p = nullptr;
@@ -80,6 +116,7 @@ struct nfftbl_plan_s {
     nfftbl::TileGeom geom{};
     int device = 0;
     int num_sms = 0;
+    int smem_optin = 0;                   // max dynamic shared memory per block
     cudaStream_t stream = nullptr;
     std::string last_error;
     long long launches = 0;
@@ -106,6 +143,8 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf hist;               // radix sort block histograms
     nfftbl::DeviceBuf tile_off;           // n_tiles + 1 (uint32)
     nfftbl::DeviceBuf work;               // WorkItem list
+    nfftbl::DeviceBuf tile_items;         // n_tiles + 1: first work item per tile
+    nfftbl::DeviceBuf part;               // spread boxes, one slot per (item, batch entry)
     nfftbl::DeviceBuf counters;           // small device scratch (ints)
     long long n_tiles = 0;
     long long n_work = 0;

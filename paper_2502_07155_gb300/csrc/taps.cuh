@@ -464,122 +464,308 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void atomic_add_c(C2<T>* p, C2<T> v);
-template <>
-__device__ __forceinline__ void atomic_add_c<float>(float2* p, float2 v) {
-    atomicAdd(p, v);
+// ---------------------------------------------------------------------------
+// Spreading (transposed short sums, the Psi^T factor of the adjoint).
+//
+// Exact accumulation: a work item's box is accumulated in 64-bit fixed
+// point in shared memory with a power-of-two quantum q = 2^(e - 62), where
+// 2^e bounds the item's total |g| times the largest product of window
+// values, so no partial sum can overflow.  Integer addition is associative,
+// so the box is exact and independent of the order in which warps add.
+//
+// Work split: nodes are sorted by cell, so runs of consecutive nodes share
+// their 2m^d taps.  A warp takes one run; lane l owns the contiguous-
+// dimension tap c = l mod 2m and a set of rows (row group l div 2m); it sums
+// the run's contributions for its taps in registers and adds each sum to
+// the box once.
+//
+// Ordered flush: the item's box (converted back to the plan's precision)
+// is stored to its own slot of a scratch array; gather_kernel then forms
+// every grid value as the sum over the boxes that cover it in a fixed
+// order (tiles in row-major order, then the tile's items in order).  No
+// global atomics, no clearing of the grid, bitwise reproducible results.
+
+template <typename T> __device__ __forceinline__ long long to_fixed(T v, T inv_q);
+template <> __device__ __forceinline__ long long to_fixed<float>(float v, float inv_q) {
+    return __float2ll_rn(v * inv_q);
 }
-template <>
-__device__ __forceinline__ void atomic_add_c<double>(double2* p, double2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
+template <> __device__ __forceinline__ long long to_fixed<double>(double v, double inv_q) {
+    return __double2ll_rn(v * inv_q);
+}
+
+__device__ __forceinline__ void fixed_add(unsigned long long* p, long long v) {
+    if (v != 0) atomicAdd(p, static_cast<unsigned long long>(v));
 }
 
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a) {
     using CT = C2<T>;
-    extern __shared__ __align__(128) unsigned char smem[];
-    CT* box = aligned_box_base<T>(smem);
-    T* boxs = reinterpret_cast<T*>(box);
-    int box_cells = 1;
-#pragma unroll
-    for (int t = 0; t < D; ++t) box_cells *= a.g.box[t];
-    const int slot = box_slot_cells<T>(box_cells);
-    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    using U = unsigned long long;
     constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     const int m = nw / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    int box_cells = 1;
+#pragma unroll
+    for (int t = 0; t < D; ++t) box_cells *= a.g.box[t];
+    const int slot = (box_cells + 1) / 2 * 2;
+    const int nbmax = a.spread_batch;
+    const int sub = a.spread_sub;
+    const SpreadSmem L = spread_smem_layout<T>(D, A, box_cells, nbmax, sub);
+    U* boxu = reinterpret_cast<U*>(smem + L.box);
+    int* s_lb = reinterpret_cast<int*>(smem + L.lb);
+    T* s_w = reinterpret_cast<T*>(smem + L.w);
+    CT* s_g = reinterpret_cast<CT*>(smem + L.g);
+    int* s_run = reinterpret_cast<int*>(smem + L.run);
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int G = 32 / nw;                       // row groups per warp
+    const int c = lane % nw;                     // owned contiguous-dimension tap
+    const int rg = lane / nw;                    // row group
+    const bool active = rg < G;
+    constexpr int RPL = W ? (W + (32 / (W ? W : 1)) - 1) / (32 / (W ? W : 1)) : 24;   // rows per lane (bound)
+    const int rpl = (nw + G - 1) / G;
+
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
         int org[3] = {0, 0, 0};
         tile_origin<D>(a.g, wi.tile, periodic, org);
-        for (int b0 = 0; b0 < a.batch; b0 += a.batch_smem) {
-            const int nb = min(a.batch_smem, a.batch - b0);
-            for (int idx = threadIdx.x; idx < nb * slot; idx += blockDim.x) box[idx] = cmake<T>(T(0), T(0));
-            __syncthreads();
-            for (int j = threadIdx.x; j < wi.count; j += blockDim.x) {
-                const long long i = static_cast<long long>(wi.start) + j;
-                T tau[3];
-                int lb[3] = {0, 0, 0};
-                node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
-                T w0[A], w1[A], w2[A];
-                tap_weights<T, W>(tau[0], a.w, w0);
-                if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
-                if (D > 2) tap_weights<T, W>(tau[2], a.w, w2);
-                const long long src = a.perm[i];
+        for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
+            const int nb = min(nbmax, a.batch - b0);
+            // ---- quantum: bound on the item's total contribution
+            double part = 0.0;
+            for (int j = tid; j < wi.count; j += blockDim.x) {
+                const long long src = a.perm[wi.start + j];
                 for (int bb = 0; bb < nb; ++bb) {
                     const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-                    T* bx = boxs + 2LL * bb * slot;
-                    if (D == 1) {
+                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+            if (lane == 0) s_red[warp] = part;
+            for (int idx = tid; idx < nb * slot * 2; idx += blockDim.x) boxu[idx] = 0ull;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+                tot *= static_cast<double>(a.wbound) * 1.0001;
+                int e = 0;
+                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e; 2^(62-e) stays a finite float
+                s_red[32] = ldexp(1.0, e - 62);                // quantum q
+                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            const double qd = s_red[32];
+            const bool any = s_red[33] != 0.0;
+            const T inv_q = static_cast<T>(1.0 / qd);
+            if (any) {
+                for (int s0 = 0; s0 < wi.count; s0 += sub) {
+                    const int ns = min(sub, wi.count - s0);
+                    // ---- per-node setup: local first tap, window factors, inputs
+                    if (tid < ns) {
+                        const long long i = static_cast<long long>(wi.start) + s0 + tid;
+                        T tau[3];
+                        int lb[3] = {0, 0, 0};
+                        node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
+                        s_lb[tid] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
+                        T wt[A];
 #pragma unroll
-                        for (int q = 0; q < nw; ++q) {
-                            const int c = lb[0] + q;
-                            atomicAdd(bx + 2 * c, gv.x * w0[q]);
-                            atomicAdd(bx + 2 * c + 1, gv.y * w0[q]);
+                        for (int t = 0; t < D; ++t) {
+                            tap_weights<T, W>(tau[t], a.w, wt);
+                            T* dst = s_w + (static_cast<size_t>(tid) * D + t) * A;
+#pragma unroll
+                            for (int q = 0; q < nw; ++q) dst[q] = wt[q];
                         }
-                    } else if (D == 2) {
-                        const int pitch = a.g.box[1];
-                        for (int q0 = 0; q0 < nw; ++q0) {
-                            const T gr = gv.x * w0[q0], gi = gv.y * w0[q0];
-                            const int rowc = (lb[0] + q0) * pitch + lb[1];
+                        const long long src = a.perm[i];
+                        for (int bb = 0; bb < nb; ++bb)
+                            s_g[bb * sub + tid] = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
+                    }
+                    __syncthreads();
+                    // ---- runs of nodes in one cell (block-wide compaction of run starts)
+                    int nruns = 0;
+                    {
+                        const int flag = (tid < ns) && (tid == 0 || s_lb[tid] != s_lb[tid - 1]);
+                        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+                        const int before = __popc(bal & ((1u << lane) - 1u));
+                        if (lane == 0) s_red[warp] = __popc(bal);
+                        __syncthreads();
+                        int wbase = 0;
+                        for (int w = 0; w < warp; ++w) wbase += static_cast<int>(s_red[w]);
+                        for (int w = 0; w < nwarps; ++w) nruns += static_cast<int>(s_red[w]);
+                        if (flag) s_run[wbase + before] = tid;
+                        if (tid == 0) s_run[nruns] = ns;
+                        __syncthreads();
+                    }
+                    // ---- accumulate runs
+                    if (active) {
+                        for (int r = warp; r < nruns; r += nwarps) {
+                            const int jlo = s_run[r], jhi = s_run[r + 1];
+                            const int lbp = s_lb[jlo];
+                            const int lb0 = lbp & 1023, lb1 = (lbp >> 10) & 1023, lb2 = lbp >> 20;
+                            for (int bb = 0; bb < nb; ++bb) {
+                                U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
+                                const CT* gg = s_g + bb * sub;
+                                if (D == 1) {
+                                    // row groups split the run's nodes; sums are exact in fixed point
+                                    T ar = T(0), ai = T(0);
+                                    for (int j = jlo + rg; j < jhi; j += G) {
+                                        const T wv = s_w[static_cast<size_t>(j) * A + c];
+                                        ar += gg[j].x * wv;
+                                        ai += gg[j].y * wv;
+                                    }
+                                    const int cell = lb0 + c;
+                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar, inv_q));
+                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai, inv_q));
+                                } else if (D == 2) {
+                                    T ar[RPL], ai[RPL];
 #pragma unroll
-                            for (int q1 = 0; q1 < nw; ++q1) {
-                                atomicAdd(bx + 2 * (rowc + q1), gr * w1[q1]);
-                                atomicAdd(bx + 2 * (rowc + q1) + 1, gi * w1[q1]);
-                            }
-                        }
-                    } else {
-                        const int p1 = a.g.box[2];
-                        const int p0 = a.g.box[1] * p1;
-                        for (int q0 = 0; q0 < nw; ++q0) {
-                            for (int q1 = 0; q1 < nw; ++q1) {
-                                const T wab = w0[q0] * w1[q1];
-                                const T gr = gv.x * wab, gi = gv.y * wab;
-                                const int rowc = (lb[0] + q0) * p0 + (lb[1] + q1) * p1 + lb[2];
+                                    for (int k = 0; k < RPL; ++k) ar[k] = ai[k] = T(0);
+                                    for (int j = jlo; j < jhi; ++j) {
+                                        const T* wj = s_w + static_cast<size_t>(j) * 2 * A;
+                                        const T wf = wj[A + c];
+                                        const T gr = gg[j].x * wf, gi = gg[j].y * wf;
 #pragma unroll
-                                for (int q2 = 0; q2 < nw; ++q2) {
-                                    atomicAdd(bx + 2 * (rowc + q2), gr * w2[q2]);
-                                    atomicAdd(bx + 2 * (rowc + q2) + 1, gi * w2[q2]);
+                                        for (int k = 0; k < RPL; ++k) {
+                                            const int row = rg + G * k;
+                                            if (k < rpl && row < nw) {
+                                                ar[k] += gr * wj[row];
+                                                ai[k] += gi * wj[row];
+                                            }
+                                        }
+                                    }
+                                    const int pitch = a.g.box[1];
+#pragma unroll
+                                    for (int k = 0; k < RPL; ++k) {
+                                        const int row = rg + G * k;
+                                        if (k < rpl && row < nw) {
+                                            const int cell = (lb0 + row) * pitch + lb1 + c;
+                                            fixed_add(bx + 2 * cell, to_fixed<T>(ar[k], inv_q));
+                                            fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[k], inv_q));
+                                        }
+                                    }
+                                } else {
+                                    const int p2 = a.g.box[2];
+                                    const int p1 = a.g.box[1] * p2;
+                                    for (int a0 = 0; a0 < nw; ++a0) {
+                                        T ar[RPL], ai[RPL];
+#pragma unroll
+                                        for (int k = 0; k < RPL; ++k) ar[k] = ai[k] = T(0);
+                                        for (int j = jlo; j < jhi; ++j) {
+                                            const T* wj = s_w + static_cast<size_t>(j) * 3 * A;
+                                            const T wf = wj[2 * A + c] * wj[a0];
+                                            const T gr = gg[j].x * wf, gi = gg[j].y * wf;
+#pragma unroll
+                                            for (int k = 0; k < RPL; ++k) {
+                                                const int row = rg + G * k;
+                                                if (k < rpl && row < nw) {
+                                                    ar[k] += gr * wj[A + row];
+                                                    ai[k] += gi * wj[A + row];
+                                                }
+                                            }
+                                        }
+#pragma unroll
+                                        for (int k = 0; k < RPL; ++k) {
+                                            const int row = rg + G * k;
+                                            if (k < rpl && row < nw) {
+                                                const int cell = (lb0 + a0) * p1 + (lb1 + row) * p2 + lb2 + c;
+                                                fixed_add(bx + 2 * cell, to_fixed<T>(ar[k], inv_q));
+                                                fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[k], inv_q));
+                                            }
+                                        }
+                                    }
                                 }
                             }
                         }
                     }
+                    __syncthreads();
                 }
             }
-            __syncthreads();
-            // flush the box into the grid: nonzero cells only; cells outside
-            // I_L are dropped (Shannon, zero extension) or wrapped (classical)
-            for (int idx = threadIdx.x; idx < nb * box_cells; idx += blockDim.x) {
+            // ---- store the item's box (plan precision) to its scratch slot
+            for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
                 const int bb = idx / box_cells;
                 const int cell = idx - bb * box_cells;
-                const CT v = box[bb * slot + cell];
-                if (v.x == T(0) && v.y == T(0)) continue;
-                int r = cell;
-                int loc[3] = {0, 0, 0};
-#pragma unroll
-                for (int t = D - 1; t >= 0; --t) {
-                    loc[t] = r % a.g.box[t];
-                    r /= a.g.box[t];
-                }
-                long long gi = 0;
-                bool inside = true;
-#pragma unroll
-                for (int t = 0; t < D; ++t) {
-                    int c = org[t] + loc[t];
-                    if (periodic) {
-                        c %= a.g.L[t];
-                        if (c < 0) c += a.g.L[t];
-                    } else if (c < 0 || c >= a.g.L[t]) {
-                        inside = false;
-                    }
-                    gi = gi * a.g.L[t] + c;
-                }
-                if (inside) atomic_add_c<T>(a.grid + (b0 + bb) * a.grid_stride + gi, v);
+                const U* u = boxu + (static_cast<size_t>(bb) * slot + cell) * 2;
+                CT v;
+                v.x = static_cast<T>(static_cast<double>(static_cast<long long>(u[0])) * qd);
+                v.y = static_cast<T>(static_cast<double>(static_cast<long long>(u[1])) * qd);
+                a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
             }
             __syncthreads();
         }
     }
+}
+
+// Ordered flush: grid[b][l] = sum over the boxes covering l, in a fixed order.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) gather_kernel(const TapArgs<T> a) {
+    using CT = C2<T>;
+    constexpr int kMaxCand = 48;   // >= 3 periodic images x (box/T + 1) tiles, T >= 2
+    const long long total = static_cast<long long>(a.batch) * a.grid_stride;
+    const long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (idx >= total) return;
+    const int b = static_cast<int>(idx / a.grid_stride);
+    long long rem = idx - static_cast<long long>(b) * a.grid_stride;
+    int gc[3] = {0, 0, 0};
+#pragma unroll
+    for (int t = D - 1; t >= 0; --t) {
+        gc[t] = static_cast<int>(rem % a.g.L[t]);
+        rem /= a.g.L[t];
+    }
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    // candidate (tile coordinate, local coordinate) pairs per dimension
+    int cand_c[3][kMaxCand], cand_l[3][kMaxCand], ncand[3] = {0, 0, 0};
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        const int T_ = a.g.T[t], box = a.g.box[t], off = a.g.off[t], L = a.g.L[t];
+        for (int k = periodic ? -1 : 0; k <= (periodic ? 1 : 0); ++k) {
+            const int gp = gc[t] + k * L;
+            // tiles c with c*T - off <= gp < c*T - off + box
+            int clo = gp + off - box + 1;
+            clo = (clo >= 0) ? (clo + T_ - 1) / T_ : -((-clo) / T_);
+            int chi = gp + off;
+            chi = (chi >= 0) ? chi / T_ : -((-chi + T_ - 1) / T_);
+            clo = max(clo, 0);
+            chi = min(chi, a.g.nt[t] - 1);
+            for (int cc = clo; cc <= chi; ++cc) {
+                if (ncand[t] < kMaxCand) {
+                    cand_c[t][ncand[t]] = cc;
+                    cand_l[t][ncand[t]] = gp - (cc * T_ - off);
+                    ncand[t]++;
+                } else {
+                    atomicOr(a.err, DEVERR_INTERNAL);
+                }
+            }
+        }
+    }
+    int box_cells = 1;
+#pragma unroll
+    for (int t = 0; t < D; ++t) box_cells *= a.g.box[t];
+    T sr = T(0), si = T(0);
+    const int n1 = D > 1 ? ncand[1] : 1, n2 = D > 2 ? ncand[2] : 1;
+    for (int i0 = 0; i0 < ncand[0]; ++i0) {
+        for (int i1 = 0; i1 < n1; ++i1) {
+            for (int i2 = 0; i2 < n2; ++i2) {
+                int tile = cand_c[0][i0];
+                int local = cand_l[0][i0];
+                if (D > 1) {
+                    tile = tile * a.g.nt[1] + cand_c[1][i1];
+                    local = local * a.g.box[1] + cand_l[1][i1];
+                }
+                if (D > 2) {
+                    tile = tile * a.g.nt[2] + cand_c[2][i2];
+                    local = local * a.g.box[2] + cand_l[2][i2];
+                }
+                const uint32_t s = a.tile_items[tile], e = a.tile_items[tile + 1];
+                for (uint32_t it = s; it < e; ++it) {
+                    const CT v = a.part[(static_cast<long long>(it) * a.batch + b) * box_cells + local];
+                    sr += v.x;
+                    si += v.y;
+                }
+            }
+        }
+    }
+    a.grid[idx] = cmake<T>(sr, si);
 }
 
 // Node gradient: grad_x[j, t] = sum_b Re(conj(gf[b, j]) * d f_{b,j} / d x_{j,t}).
@@ -675,7 +861,8 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     if (occ < 1) return fail(p, NFFTBL_EUNSUPPORTED, "tap kernel does not fit on an SM");
     const long long want = static_cast<long long>(occ) * p->num_sms;
     const unsigned grid = static_cast<unsigned>(std::max<long long>(1, std::min<long long>(want, args.n_work)));
-    if (args.n_work == 0) return NFFTBL_OK;
+    // (with no work items the spread kernel's CTAs exit at once; the gather still clears the grid)
+    if (args.n_work == 0 && kind != TAP_SPREAD) return NFFTBL_OK;
     timing_begin(p, kind == TAP_INTERP ? NFFTBL_K_INTERP : kind == TAP_SPREAD ? NFFTBL_K_SPREAD : NFFTBL_K_GRAD);
     if (kind == TAP_INTERP)
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
@@ -685,7 +872,15 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         node_grad_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
     timing_end(p);
     p->launches++;
-    return check_cuda(p, cudaGetLastError(), "tap kernel launch");
+    st = check_cuda(p, cudaGetLastError(), "tap kernel launch");
+    if (st != NFFTBL_OK || kind != TAP_SPREAD) return st;
+    // ordered flush of the spread boxes into the grid
+    const long long cells = static_cast<long long>(args.batch) * args.grid_stride;
+    timing_begin(p, NFFTBL_K_FLUSH);
+    gather_kernel<T, D><<<static_cast<unsigned>((cells + 255) / 256), 256, 0, p->stream>>>(args);
+    timing_end(p);
+    p->launches++;
+    return check_cuda(p, cudaGetLastError(), "gather kernel launch");
 }
 
 }  // namespace nfftbl

@@ -216,3 +216,44 @@ def test_kernel_launch_count_grows():
     plan.forward(to_dev(W.fhat_gaussian(plan.M, dtype=np.complex64)))
     plan.sync()
     assert plan.kernel_launches() == n0 + 3     # two FFT passes + interpolation
+
+
+# --------------------------------------------------------------------------- adjoint: exactness and dense cells
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_adjoint_bitwise_deterministic(prec):
+    """Fixed-point box accumulation and the ordered flush make the adjoint
+    independent of scheduling: repeated calls agree bit for bit."""
+    plan, x = make(3, prec, batch=2, N=5000)
+    g = to_dev(W.adjoint_input(x.shape[0], batch=2, dtype=CDT[prec]))
+    h1 = to_host(plan.adjoint(g))
+    h2 = to_host(plan.adjoint(g))
+    np.testing.assert_array_equal(h1, h2)
+
+
+def clustered_nodes(n, d, dtype, seed=7):
+    """Most nodes in a few cells near the origin (long same-cell runs, many
+    work items per tile), the rest uniform: the radial-spoke centre in
+    miniature."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-0.5, 0.5, size=(n, d))
+    k = int(0.8 * n)
+    x[:k] = rng.normal(0.0, 2e-3, size=(k, d))
+    return np.clip(x, -0.5, np.nextafter(0.5, 0)).astype(dtype)
+
+
+@pytest.mark.parametrize("d,prec,method", [(2, "f32", "shannon"), (3, "f32", "shannon"), (2, "f64", "shannon"),
+                                           (3, "f64", "classic"), (1, "f32", "shannon")])
+def test_adjoint_dense_cells(d, prec, method):
+    M = {1: 256, 2: 64, 3: 32}[d]
+    m = {1: 8, 2: 6, 3: 4}[d]
+    plan = nb.Plan(d, M, 2.0, m, precision=prec, method=method, batch=1, nodes_per_item=256)
+    x = clustered_nodes(6000, d, RDT[prec])
+    plan.set_nodes(to_dev(x))
+    assert plan.info()["n_work"] > plan.info()["n_tiles"] // 8   # several items in the dense tiles
+    g = W.adjoint_input(x.shape[0], dtype=CDT[prec])
+    h = to_host(plan.adjoint(to_dev(g)))
+    ref = O.adjoint(oracle_plan(plan), g, x)
+    assert rel_l2(h, ref) < TOL[prec]
+    f = to_host(plan.forward(to_dev(W.fhat_gaussian(plan.M, dtype=CDT[prec]))))
+    assert np.all(np.isfinite(f))
