@@ -446,6 +446,90 @@ def run_ours(args, cfg):
     return 0
 
 
+def run_learned(args):
+    """Learned window at d = 2, M = 256, sigma = 2: train phi_theta on 2^16
+    feasible uniform nodes (Fourier data N(0,1) x triangle), then compare with
+    the sinh window on 2^22 held-out nodes at equal m and by the m each needs
+    for a given error.  Targets are the trigonometric sums, computed by the
+    FP64 classical NFFT at m = 12 (equal to the NDFT to ~1e-14)."""
+    import torch
+    from paper_2502_07155_gb300 import build
+    build.build()
+    import paper_2502_07155_gb300 as nb
+    from paper_2502_07155_gb300.learned import WindowTrainer
+
+    d, M = 2, 256
+    L = 2 * M
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+
+    def targets(x, fh):
+        ref = nb.Plan(d, M, 2.0, 12, precision="f64", method="classic")
+        ref.set_nodes(torch.from_numpy(x.astype(np.float64)).to(dev))
+        out = ref.forward(torch.from_numpy(fh.astype(np.complex128)).to(dev))
+        ref.close()
+        return out
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a.to(torch.complex128) - b) / torch.linalg.vector_norm(b))
+
+    def fwd_time(plan, fh_d, out):
+        for _ in range(3):
+            plan.forward(fh_d, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            plan.forward(fh_d, out=out)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 10
+
+    results = []
+    for m in args.learned_m:
+        xt = W.nodes_feasible(1 << 16, d, m, L, seed=W.SEED_TRAIN)
+        fht = W.fhat_gaussian(M, d, seed=W.SEED_TRAIN)
+        yt = targets(xt, fht).to(torch.complex64)
+        tr = WindowTrainer(d, M, m, lr=args.learned_lr)
+        tr.set_data(torch.from_numpy(xt).to(dev), torch.from_numpy(fht).to(dev), yt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = tr.train(args.learned_steps, log_every=max(1, args.learned_steps // 5))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        tab = tr.table_host()
+        # held-out nodes feasible for the largest m compared (m + 2)
+        xh = W.nodes_feasible(1 << 22, d, m + 2, L, seed=W.SEED_HELDOUT)
+        fhh = W.fhat_gaussian(M, d, seed=W.SEED_HELDOUT)
+        yh = targets(xh, fhh)
+        xh_d = torch.from_numpy(xh).to(dev)
+        fhh_d = torch.from_numpy(fhh).to(dev)
+        out = torch.empty((1, xh.shape[0]), dtype=torch.complex64, device=dev)
+        row = {"m": m, "train_steps": args.learned_steps, "train_seconds": t_train,
+               "train_loss": [[i, v] for i, v in hist]}
+        pl = nb.Plan(d, M, 2.0, m, window="table", table=tab, precision="f32")
+        pl.set_nodes(xh_d)
+        row["learned_err"] = rel(pl.forward(fhh_d, out=out), yh)
+        row["learned_fwd_ms"] = fwd_time(pl, fhh_d, out)
+        pl.close()
+        sinh = {}
+        for ms in sorted(set([m, m + 1, m + 2])):
+            ps = nb.Plan(d, M, 2.0, ms, precision="f32")
+            ps.set_nodes(xh_d)
+            sinh[ms] = {"err": rel(ps.forward(fhh_d, out=out), yh), "fwd_ms": fwd_time(ps, fhh_d, out)}
+            ps.close()
+        row["sinh"] = sinh
+        row["gain_equal_m"] = sinh[m]["err"] / row["learned_err"]
+        results.append(row)
+        print(json.dumps(row), file=sys.stderr)
+    out = {"metric": "learned window vs sinh window: held-out relative l2 error against the trigonometric sum",
+           "config": {"workload": "learned_window_d2_M256_sigma2", "train_nodes": 1 << 16, "heldout_nodes": 1 << 22,
+                      "targets": "FP64 classical NFFT m=12", "mlp": "1-64-64-1 tanh, BF16 backward",
+                      "table_len": 4097},
+           "results": results, "data": "synthetic", "n_gpus": 1}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,6 +537,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default=DEFAULT_CONFIG)
+    ap.add_argument("--learned", action="store_true", help="train and evaluate the learned window (d=2, M=256)")
+    ap.add_argument("--learned-m", type=int, nargs="+", default=[2, 3, 4], dest="learned_m")
+    ap.add_argument("--learned-steps", type=int, default=1500, dest="learned_steps")
+    ap.add_argument("--learned-lr", type=float, default=3e-3, dest="learned_lr")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no FP64, classical, end-to-end or oracle legs); for profiling")
     args = ap.parse_args()
@@ -460,6 +548,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args, args.config)
+    if args.learned:
+        return run_learned(args)
     return run_ours(args, args.config)
 
 

@@ -250,6 +250,64 @@ nfftbl_status nfftbl_kernel_timing(nfftbl_plan_t plan, int enable);
 nfftbl_status nfftbl_kernel_times(nfftbl_plan_t plan, double* ms_out, int64_t* count_out);
 
 /* ---------------------------------------------------------------------------
+ * Learned window (tabulated window trained on the transform's own error).
+ *
+ * The window class Phi_{m,L} of Section 3 admits windows other than the two
+ * of Remark 3.1; these calls let a tabulated window phi(u), u = |Lx|/m, be
+ * produced by a small MLP and trained on the device:
+ *   phi_theta(u) = (1 - u^2) exp(g(u^2) - g(0)),
+ *   g(s) = W3 tanh(W2 tanh(W1 s + b1) + b2) + b3   (1 -> 64 -> 64 -> 1).
+ * Parameter layout (float): W1[64], b1[64], W2[64][64] (out x in), b2[64],
+ * W3[64], b3[1] (nfftbl_mlp_param_count(64) values).
+ * ------------------------------------------------------------------------ */
+
+/* Replace the plan's table (plan made with NFFTBL_WIN_TABLE) by table_len
+ * doubles in device memory and recompute psi_hat and D_psihat (Alg. 4.2
+ * step 0a) on the plan's stream.  No allocation.  Errors: EINVAL (length
+ * differs from the plan's), ESTATE (not a table window), ECUDA. */
+nfftbl_status nfftbl_set_window_table(nfftbl_plan_t plan, const double* table_dev, int table_len);
+
+/* Loss of the transform against targets and its gradient with respect to
+ * the window table (FP32 Shannon plans with a table window, d <= 2):
+ *   E = ||f - y||^2 / ||y||^2,   f = Psi F D_psihat fhat (Eq. 4.11),
+ * dE/dv through both the short-sum weights and the precorrection (the
+ * quadrature that forms psi_hat from the table).
+ *   fhat_dev       : B x prod(M_t) complex64;   y_dev : B x N complex64 (caller order);
+ *   grad_table_dev : table_len doubles (overwritten);
+ *   loss_dev       : 3 doubles (overwritten): E, ||f - y||^2, ||y||^2.
+ * Overwrites the plan's grid.  Asynchronous.  Errors: ESTATE (no nodes, not a
+ * Shannon table plan), EUNSUPPORTED (FP64 or d = 3), ENOMEM, ECUDA. */
+nfftbl_status nfftbl_window_loss_grad(nfftbl_plan_t plan, const void* fhat_dev, const void* y_dev,
+                                      double* grad_table_dev, double* loss_dev);
+
+/* Evaluate the MLP at u_i = i/(table_len-1) and write the window table
+ * (doubles, device).  act_dev receives the activations the backward pass
+ * needs: table_len * (2*hidden + 1) floats.  FP32 arithmetic.  hidden must be
+ * 64 (EUNSUPPORTED otherwise). */
+nfftbl_status nfftbl_mlp_table(const float* params_dev, int hidden, int table_len, double* table_dev,
+                               float* act_dev, void* cuda_stream);
+
+/* Gradient of the loss with respect to the MLP parameters from its gradient
+ * with respect to the table (chain rule through v_i = (1-u_i^2) exp(g_i - g_0)
+ * and back-propagation through the MLP; the two 64-wide matrix products run
+ * on the tensor cores in BF16 with FP32 accumulation).  scratch_dev: at least
+ * nfftbl_mlp_scratch_floats(hidden, table_len) floats; grad_params_dev:
+ * nfftbl_mlp_param_count(hidden) floats (overwritten). */
+nfftbl_status nfftbl_mlp_backward(const float* params_dev, int hidden, int table_len, const float* act_dev,
+                                  const double* table_dev, const double* grad_table_dev, float* scratch_dev,
+                                  float* grad_params_dev, void* cuda_stream);
+
+/* Parameter count of the MLP (-1 if hidden != 64) and scratch size (floats)
+ * of nfftbl_mlp_backward (-1 if unsupported). */
+int64_t nfftbl_mlp_param_count(int hidden);
+int64_t nfftbl_mlp_scratch_floats(int hidden, int table_len);
+
+/* One Adam step (bias-corrected, step >= 1) on count parameters, all device
+ * arrays of floats: params -= lr * mhat / (sqrt(vhat) + eps). */
+nfftbl_status nfftbl_adam_step(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int count,
+                               int step, float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free equispaced samples.
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -24,7 +24,7 @@ from scipy import integrate, special
 __all__ = [
     "oversampled_length", "default_beta", "Window", "Plan", "make_plan",
     "sinc", "dsinc", "window_transform", "precorrection_factors",
-    "fourier_matrix", "step1_precorrect", "step2_idft", "step3_short_sums",
+    "fourier_matrix", "step1_precorrect", "mlp_backward", "learned_table_grad", "window_loss", "step2_idft", "step3_short_sums",
     "forward", "grid_samples", "adjoint", "adjoint_short_sums",
     "adjoint_idft", "ndft", "ndft_adjoint", "node_derivative", "node_grad",
     "bin_nodes", "tap_ranges", "dense_matrices", "mlp_init", "mlp_forward",
@@ -657,3 +657,41 @@ def learned_table(params, n: int = 4096) -> np.ndarray:
     g = mlp_forward(params, u * u)
     g0 = mlp_forward(params, np.zeros(1))[0]
     return (1.0 - u * u) * np.exp(g - g0)
+
+
+def mlp_backward(params, s: np.ndarray, upstream: np.ndarray):
+    """Gradient of sum_i upstream_i * g(s_i) with respect to the MLP
+    parameters (plain backpropagation in FP64)."""
+    s = np.asarray(s, dtype=np.float64).reshape(-1, 1)
+    up = np.asarray(upstream, dtype=np.float64).reshape(-1, 1)
+    z1 = s @ params["W1"].T + params["b1"]
+    h1 = np.tanh(z1)
+    z2 = h1 @ params["W2"].T + params["b2"]
+    h2 = np.tanh(z2)
+    grads = {"W3": up.T @ h2, "b3": up.sum(axis=0)}
+    d2 = (up @ params["W3"]) * (1.0 - h2 * h2)
+    grads["W2"] = d2.T @ h1
+    grads["b2"] = d2.sum(axis=0)
+    d1 = (d2 @ params["W2"]) * (1.0 - h1 * h1)
+    grads["W1"] = d1.T @ s
+    grads["b1"] = d1.sum(axis=0)
+    return grads
+
+
+def learned_table_grad(params, dE_dv: np.ndarray, n: int = 4096):
+    """Chain rule from a gradient with respect to the table values
+    v_i = (1 - u_i^2) exp(g(u_i^2) - g(0)) to the MLP parameters."""
+    u = np.arange(n + 1, dtype=np.float64) / n
+    v = learned_table(params, n)
+    up = np.asarray(dE_dv, dtype=np.float64) * v          # d v_i / d g(u_i^2) = v_i
+    grads = mlp_backward(params, u * u, up)
+    g0 = mlp_backward(params, np.zeros(1), np.array([-np.sum(up)]))   # d v_i / d g(0) = -v_i
+    return {k: grads[k] + g0[k] for k in grads}
+
+
+def window_loss(plan: Plan, fhat: np.ndarray, x: np.ndarray, y: np.ndarray, factors=None) -> float:
+    """E = ||f - y||^2 / ||y||^2 with f the forward transform of ``plan``
+    (the objective of the learned window; y is the trigonometric sum)."""
+    f = forward(plan, fhat, x, factors)
+    y = np.asarray(y, dtype=np.complex128)
+    return float(np.sum(np.abs(f - y) ** 2) / np.sum(np.abs(y) ** 2))

@@ -36,6 +36,8 @@ EXPORTED = [
     "nfftbl_plan_error", "nfftbl_get_info", "nfftbl_get_factors", "nfftbl_get_binning", "nfftbl_get_grid",
     "nfftbl_grid_ptr", "nfftbl_interp_grid", "nfftbl_spread_grid", "nfftbl_kernel_launches",
     "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
+    "nfftbl_set_window_table", "nfftbl_window_loss_grad", "nfftbl_mlp_table", "nfftbl_mlp_backward",
+    "nfftbl_mlp_param_count", "nfftbl_mlp_scratch_floats", "nfftbl_adam_step",
 ]
 KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin", "flush")
 
@@ -119,6 +121,21 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_grid_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_int, P, P, P]
     L.nfftbl_grid_noalloc.restype = st
+    L.nfftbl_set_window_table.argtypes = [P, P, ctypes.c_int]
+    L.nfftbl_set_window_table.restype = st
+    L.nfftbl_window_loss_grad.argtypes = [P, P, P, P, P]
+    L.nfftbl_window_loss_grad.restype = st
+    L.nfftbl_mlp_table.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
+    L.nfftbl_mlp_table.restype = st
+    L.nfftbl_mlp_backward.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
+    L.nfftbl_mlp_backward.restype = st
+    L.nfftbl_mlp_param_count.argtypes = [ctypes.c_int]
+    L.nfftbl_mlp_param_count.restype = ctypes.c_int64
+    L.nfftbl_mlp_scratch_floats.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.nfftbl_mlp_scratch_floats.restype = ctypes.c_int64
+    L.nfftbl_adam_step.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, P]
+    L.nfftbl_adam_step.restype = st
     _lib = L
     return L
 
@@ -323,6 +340,23 @@ class Plan:
         out = np.empty((self.batch,) + self.L, dtype=dt)
         self._check(self._lib.nfftbl_get_grid(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+    def set_window_table(self, table_dev):
+        """Replace the table window by a (len,) float64 CUDA tensor."""
+        t = self._dev(table_dev, _torch().float64, name="table")
+        self._stream()
+        self._check(self._lib.nfftbl_set_window_table(self._h, t, int(table_dev.numel())))
+
+    def window_loss_grad(self, fhat, y, grad_table, loss):
+        """E = ||f - y||^2/||y||^2 and dE/d(table) into the given float64 CUDA
+        tensors (grad_table: (len,), loss: (3,) = E, num, den)."""
+        torch = _torch()
+        fh = self._dev(fhat, self._cdtype, (self.batch,) + self.M, "fhat")
+        yy = self._dev(y, self._cdtype, (self.batch, max(self.n_nodes, 0)), "y")
+        gt = self._dev(grad_table, torch.float64, name="grad_table")
+        ls = self._dev(loss, torch.float64, (3,), "loss")
+        self._stream()
+        self._check(self._lib.nfftbl_window_loss_grad(self._h, fh, yy, gt, ls))
 
     def kernel_launches(self) -> int:
         return int(self._lib.nfftbl_kernel_launches(self._h))

@@ -119,4 +119,26 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Add val * d(table(u))/d(v_i) to tab_grad for the four entries of the
+// Catmull-Rom stencil at u in [0, 1] (table v_0..v_n, ghost values
+// v_{-1} = v_1 and v_{n+1} = 2 v_n - v_{n-1} folded back).
+__device__ __forceinline__ void scatter_catmull(double* tab_grad, int n, double u, double val) {
+    const double s = fmin(fmax(u, 0.0), 1.0) * n;
+    const int i = min(static_cast<int>(floor(s)), n - 1);
+    const double t = s - i;
+    const double c0 = 0.5 * (-t + 2.0 * t * t - t * t * t);
+    const double c1 = 0.5 * (2.0 - 5.0 * t * t + 3.0 * t * t * t);
+    const double c2 = 0.5 * (t + 4.0 * t * t - 3.0 * t * t * t);
+    const double c3 = 0.5 * (-t * t + t * t * t);
+    atomicAdd(&tab_grad[(i == 0) ? 1 : i - 1], val * c0);
+    atomicAdd(&tab_grad[i], val * c1);
+    atomicAdd(&tab_grad[i + 1], val * c2);
+    if (i + 2 <= n) {
+        atomicAdd(&tab_grad[i + 2], val * c3);
+    } else {
+        atomicAdd(&tab_grad[n], 2.0 * val * c3);
+        atomicAdd(&tab_grad[n - 1], -val * c3);
+    }
+}
+
 }  // namespace nfftbl

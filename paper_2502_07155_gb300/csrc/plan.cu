@@ -171,6 +171,16 @@ bool spread_config(const nfftbl_plan_s* p, int& nb, int& sub, size_t& bytes) {
     return true;
 }
 
+}  // namespace
+
+template <typename T>
+TapArgs<T> make_tap_args_public(nfftbl_plan_s* p) {
+    return make_tap_args<T>(p);
+}
+template TapArgs<float> make_tap_args_public<float>(nfftbl_plan_s*);
+
+namespace {
+
 template <typename T>
 nfftbl_status run_taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, void* gradx) {
     TapArgs<T> a = make_tap_args<T>(p);
@@ -222,6 +232,10 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->tile_items);
     free_buf(p->part);
     free_buf(p->counters);
+    free_buf(p->lw_f);
+    free_buf(p->lw_h);
+    free_buf(p->lw_marg);
+    free_buf(p->lw_dpsi);
     free_buf(p->err);
     if (p->err_host) cudaFreeHost(p->err_host);
     for (auto& t : p->timed) {
@@ -645,6 +659,105 @@ nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t p, void** grid_dev) {
 }
 
 int64_t nfftbl_kernel_launches(nfftbl_plan_t p) { return p ? p->launches : 0; }
+
+nfftbl_status nfftbl_set_window_table(nfftbl_plan_t p, const double* table_dev, int table_len) {
+    if (!p || !table_dev) return NFFTBL_EINVAL;
+    if (p->window != NFFTBL_WIN_TABLE) return fail(p, NFFTBL_ESTATE, "plan does not use a table window");
+    if (table_len != static_cast<int>(p->table_host.size()))
+        return fail(p, NFFTBL_EINVAL, "table length differs from the plan's");
+    const bool dbl = p->precision == NFFTBL_F64;
+    void* t64 = dbl ? p->table_dev.p : p->table_dev64.p;
+    nfftbl_status st = check_cuda(p, cudaMemcpyAsync(t64, table_dev, table_len * sizeof(double),
+                                                     cudaMemcpyDeviceToDevice, p->stream),
+                                  "table copy");
+    if (st != NFFTBL_OK) return st;
+    if (!dbl &&
+        (st = check_cuda(p, launch_table_cast(static_cast<const double*>(t64), table_len,
+                                              static_cast<float*>(p->table_dev.p), p->stream),
+                         "table cast")) != NFFTBL_OK)
+        return st;
+    for (int t = 0; t < p->d; ++t) {
+        if ((st = check_cuda(p, launch_window_factors(1, NFFTBL_WIN_TABLE, p->L[t], p->M[t], p->m, p->beta,
+                                                      static_cast<const double*>(t64), table_len - 1,
+                                                      static_cast<double*>(p->fac64[t].p), p->stream),
+                             "window factors")) != NFFTBL_OK)
+            return st;
+        if ((st = check_cuda(p, launch_cast_factors(static_cast<double*>(p->fac64[t].p), p->M[t], p->facT[t].p, dbl,
+                                                    p->stream),
+                             "factor cast")) != NFFTBL_OK)
+            return st;
+        p->launches += 2;
+    }
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_window_loss_grad(nfftbl_plan_t p, const void* fhat_dev, const void* y_dev,
+                                      double* grad_table_dev, double* loss_dev) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_dev || !y_dev || !grad_table_dev || !loss_dev) return fail(p, NFFTBL_EINVAL, "NULL pointer");
+    if (p->window != NFFTBL_WIN_TABLE || p->method != NFFTBL_SHANNON)
+        return fail(p, NFFTBL_ESTATE, "window gradients need a Shannon plan with a table window");
+    if (p->precision == NFFTBL_F64 || p->d > 2)
+        return fail(p, NFFTBL_EUNSUPPORTED, "window gradients are built for FP32 plans with d <= 2");
+    const long long B = p->batch, N = p->N;
+    long long pm = 1;
+    int msum = 0;
+    for (int t = 0; t < p->d; ++t) {
+        pm *= p->M[t];
+        msum += p->M[t];
+    }
+    if ((st = ensure_buf(p, p->lw_f, B * N * 8)) != NFFTBL_OK) return st;
+    if ((st = ensure_buf(p, p->lw_h, B * pm * 8)) != NFFTBL_OK) return st;
+    if ((st = ensure_buf(p, p->lw_marg, msum * 8)) != NFFTBL_OK) return st;
+    if ((st = ensure_buf(p, p->lw_dpsi, msum * 8)) != NFFTBL_OK) return st;
+    const int n = static_cast<int>(p->table_host.size()) - 1;
+    cudaStream_t s = p->stream;
+    if ((st = check_cuda(p, cudaMemsetAsync(loss_dev, 0, 3 * sizeof(double), s), "clear loss")) != NFFTBL_OK)
+        return st;
+    if ((st = check_cuda(p, cudaMemsetAsync(grad_table_dev, 0, (n + 1) * sizeof(double), s), "clear grad")) !=
+        NFFTBL_OK)
+        return st;
+    if ((st = check_cuda(p, cudaMemsetAsync(p->lw_marg.p, 0, msum * 8, s), "clear marginals")) != NFFTBL_OK)
+        return st;
+    // forward into the scratch f, then r = f - y in place and the loss
+    if ((st = fft_forward(p, fhat_dev)) != NFFTBL_OK) return st;
+    if ((st = taps(p, TAP_INTERP, nullptr, p->lw_f.p, nullptr)) != NFFTBL_OK) return st;
+    if ((st = check_cuda(p, launch_residual(0, p->lw_f.p, y_dev, B * N, loss_dev, s), "residual")) != NFFTBL_OK)
+        return st;
+    // (A) through the tap weights (the grid still holds vartheta)
+    TapArgs<float> a = make_tap_args<float>(p);
+    a.fin = static_cast<const float2*>(p->lw_f.p);
+    if ((st = run_table_grad(p, a, loss_dev, grad_table_dev)) != NFFTBL_OK) return st;
+    // (B) through the precorrection: hhat = D F^H Psi^T r, marginals, quadrature
+    if ((st = taps(p, TAP_SPREAD, p->lw_f.p, nullptr, nullptr)) != NFFTBL_OK) return st;
+    if ((st = fft_adjoint(p, p->lw_h.p)) != NFFTBL_OK) return st;
+    double* marg = static_cast<double*>(p->lw_marg.p);
+    double* dpsi = static_cast<double*>(p->lw_dpsi.p);
+    double* Pt[3] = {marg, marg, marg};
+    int off = 0;
+    for (int t = 0; t < p->d; ++t) {
+        Pt[t] = marg + off;
+        off += p->M[t];
+    }
+    if ((st = check_cuda(p, launch_marginals(0, p->lw_h.p, fhat_dev, B * pm, p->d, p->M, Pt[0], Pt[1], Pt[2], s),
+                         "marginals")) != NFFTBL_OK)
+        return st;
+    off = 0;
+    for (int t = 0; t < p->d; ++t) {
+        if ((st = check_cuda(p, launch_dEdpsihat(marg + off, static_cast<const double*>(p->fac64[t].p), p->M[t], p->L[t],
+                                                 loss_dev, dpsi + off, s),
+                             "dE/dpsihat")) != NFFTBL_OK)
+            return st;
+        if ((st = check_cuda(p, launch_window_table_grad(p->L[t], p->M[t], p->m, n, dpsi + off, grad_table_dev, s),
+                             "quadrature gradient")) != NFFTBL_OK)
+            return st;
+        off += p->M[t];
+        p->launches += 2;
+    }
+    p->launches += 3;
+    return NFFTBL_OK;
+}
 
 nfftbl_status nfftbl_kernel_timing(nfftbl_plan_t p, int enable) {
     if (!p) return NFFTBL_EINVAL;

@@ -150,6 +150,7 @@ struct nfftbl_plan_s {
     long long n_work = 0;
     int key_bits = 0;
 
+    nfftbl::DeviceBuf lw_f, lw_h, lw_marg, lw_dpsi;   // learned-window loss/gradient scratch
     nfftbl::DeviceBuf err;                // device error word
     int* err_host = nullptr;              // pinned mirror
 
@@ -185,6 +186,17 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
 cudaError_t launch_cast_factors(const double* fac64, int M, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_table_cast(const double* in, int n, float* out, cudaStream_t s);
+cudaError_t launch_window_table_grad(int L, int M, int m, int table_n, const double* dEdpsi, double* grad,
+                                     cudaStream_t s);
+
+// learn.cu
+nfftbl_status run_table_grad(nfftbl_plan_s* p, const TapArgs<float>& args, const double* loss, double* grad);
+cudaError_t launch_residual(int is_double, void* f, const void* y, long long n, double* loss, cudaStream_t s);
+cudaError_t launch_marginals(int is_double, const void* hhat, const void* fhat, long long total, int d, const int* M,
+                             double* P0, double* P1, double* P2, cudaStream_t s);
+cudaError_t launch_dEdpsihat(const double* P, const double* fac, int M, int L, const double* loss, double* out,
+                             cudaStream_t s);
+template <typename T> TapArgs<T> make_tap_args_public(nfftbl_plan_s* p);
 
 // bin.cu
 nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev);

@@ -143,6 +143,33 @@ __global__ void table_cast_kernel(const double* __restrict__ in, int n, float* _
 
 bool g_gl_uploaded = false;
 
+constexpr int kTablePanels = 1024;   // panels of the rule for tabulated windows
+
+// Part (B) of the table-window loss gradient: psi_hat_t(q) is the same
+// quadrature as window_factor_kernel, linear in the table, so
+//   dE/dv_i = sum_q dE/dpsi_hat(q) sum_p 2 w_p sinc(pi m sin th_p) cos(2 pi q x_p) c_i(sin th_p)
+// with c_i the Catmull-Rom weights; one thread per quadrature point.
+__global__ void window_table_grad_kernel(int L, int M, int m, int table_n, int panels,
+                                         const double* __restrict__ dEdpsi, double* __restrict__ grad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= panels * kGLOrder) return;
+    const int pnl = p / kGLOrder;
+    const int q = p - pnl * kGLOrder;
+    const double h = 0.5 * M_PI / panels;
+    const double th = pnl * h + 0.5 * h * (c_gl_x[q] + 1.0);
+    double st, ct;
+    sincos(th, &st, &ct);
+    const double ml = static_cast<double>(m) / L;
+    const double x = ml * st;
+    const double z = m * st;
+    const double sincv = (z == 0.0) ? 1.0 : sinpi(z) / (M_PI * z);
+    const double wp = ml * ct * 0.5 * h * c_gl_w[q];
+    double G = 0.0;
+    for (int k = 0; k < M; ++k) G += dEdpsi[k] * 2.0 * cospi(2.0 * (k - M / 2) * x);
+    const double gamma = wp * sincv * G;
+    if (gamma != 0.0) scatter_catmull(grad, table_n, st, gamma);
+}
+
 }  // namespace
 
 cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m, double beta,
@@ -154,8 +181,19 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
     if (e != cudaSuccess) return e;
     g_gl_uploaded = true;
     // a tabulated window is only piecewise cubic: more panels
-    const int panels = (window == NFFTBL_WIN_TABLE) ? 1024 : 96;
+    const int panels = (window == NFFTBL_WIN_TABLE) ? kTablePanels : 96;
     window_factor_kernel<<<M, 256, 0, s>>>(with_sinc, window, L, M, m, beta, table, table_n, panels, fac64_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_table_grad(int L, int M, int m, int table_n, const double* dEdpsi, double* grad,
+                                     cudaStream_t s) {
+    static GLRule rule;
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, rule.x, sizeof(rule.x), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gl_w, rule.w, sizeof(rule.w), 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int pts = kTablePanels * kGLOrder;
+    window_table_grad_kernel<<<(pts + 255) / 256, 256, 0, s>>>(L, M, m, table_n, kTablePanels, dEdpsi, grad);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,139 @@
+"""Learned window: the MLP table, its backward pass, the loss gradient with
+respect to the table, and a training run, against the FP64 oracle.
+
+The MLP forward is FP32 (parity 1e-5 against FP64); its backward uses BF16
+tensor-core products with FP32 accumulation (parity a few 1e-3 relative).
+The table gradient is checked as directional derivatives against central
+differences of the oracle's loss (its own psi_hat quadrature, FP64 sums).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import rel_l2, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+nb = pytest.importorskip("paper_2502_07155_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2502_07155_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu_table(params_flat, n=4096):
+    import ctypes
+    lib = nb.lib()
+    p = to_dev(params_flat.astype(np.float32))
+    tab = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    act = torch.zeros((n + 1) * 129, dtype=torch.float32, device="cuda")
+    st = lib.nfftbl_mlp_table(ctypes.c_void_p(p.data_ptr()), 64, n + 1, ctypes.c_void_p(tab.data_ptr()),
+                              ctypes.c_void_p(act.data_ptr()), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    return p, tab, act
+
+
+def test_mlp_table_matches_oracle():
+    from paper_2502_07155_gb300.learned import init_params, params_to_dict
+    pf = init_params(seed=7)
+    pf[-65:-1] *= 100.0          # a non-trivial window: larger output weights
+    _, tab, _ = gpu_table(pf)
+    ref = O.learned_table(params_to_dict(pf))
+    got = to_host(tab)
+    assert got[0] == pytest.approx(1.0, abs=1e-12) and got[-1] == 0.0
+    assert np.max(np.abs(got - ref)) < 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kind,tol_bf16", [("smooth", 1e-2), ("oscillating", 5e-2)])
+def test_mlp_backward_matches_oracle(kind, tol_bf16):
+    import ctypes
+    from paper_2502_07155_gb300.learned import init_params, params_to_dict
+    lib = nb.lib()
+    n = 4096
+    pf = init_params(seed=7)
+    pf[-65:-1] *= 100.0
+    p, tab, act = gpu_table(pf, n)
+    i = np.arange(n + 1)
+    # a smooth positive upstream gradient, and an oscillating one whose sums
+    # over the 4097 points cancel heavily (BF16 rounding then shows more)
+    dEdv = np.exp(-i / 3000.0) if kind == "smooth" else np.cos(i * 0.013) * np.exp(-i / 3000.0)
+    gt = to_dev(dEdv)
+    count = int(lib.nfftbl_mlp_param_count(64))
+    scratch = torch.zeros(int(lib.nfftbl_mlp_scratch_floats(64, n + 1)), dtype=torch.float32, device="cuda")
+    grad = torch.zeros(count, dtype=torch.float32, device="cuda")
+    st = lib.nfftbl_mlp_backward(ctypes.c_void_p(p.data_ptr()), 64, n + 1, ctypes.c_void_p(act.data_ptr()),
+                                 ctypes.c_void_p(tab.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
+                                 ctypes.c_void_p(scratch.data_ptr()), ctypes.c_void_p(grad.data_ptr()), None)
+    assert st == 0
+    got = params_to_dict(to_host(grad))
+    ref = O.learned_table_grad(params_to_dict(pf), dEdv, n)
+    scale = np.sqrt(sum(np.sum(v ** 2) for v in ref.values()))
+    for name in ref:
+        tol = tol_bf16 if name in ("W1", "b1", "W2") else 1e-4   # BF16 products feed W1, b1, W2
+        # d/db3 is exactly zero (b3 cancels in g(u^2) - g(0)): normalise by the full gradient
+        err = np.linalg.norm(got[name].reshape(-1) - ref[name].reshape(-1))
+        assert err < tol * max(np.linalg.norm(ref[name]), 1e-3 * scale), name
+
+
+@pytest.mark.parametrize("d,M,m", [(1, 64, 2), (2, 32, 2), (2, 32, 3)])
+def test_window_loss_gradient_directional(d, M, m):
+    from paper_2502_07155_gb300.learned import init_params, params_to_dict
+    pf = init_params(seed=11)
+    pf[-65:-1] *= 50.0
+    tab_np = O.learned_table(params_to_dict(pf))
+    L = 2 * M
+    x = W.nodes_feasible(600, d, m, L, seed=5)
+    fh = W.fhat_gaussian(M, d, dtype=np.complex64)
+    y = O.ndft(fh, x).astype(np.complex64)
+    plan = nb.Plan(d, M, 2.0, m, window="table", table=tab_np, precision="f32")
+    plan.set_nodes(to_dev(x))
+    plan.set_window_table(to_dev(tab_np))
+    g = torch.zeros(tab_np.size, dtype=torch.float64, device="cuda")
+    loss = torch.zeros(3, dtype=torch.float64, device="cuda")
+    plan.window_loss_grad(to_dev(fh), to_dev(y), g, loss)
+    plan.sync()
+    grad = to_host(g)
+    op = O.make_plan(d, M, 2.0, m, window="table", table=tab_np)
+    E = O.window_loss(op, fh, x, y)
+    assert float(loss[0]) == pytest.approx(E, rel=2e-3)
+    u = np.arange(tab_np.size) / (tab_np.size - 1)
+    for k, (a, b) in enumerate([(1.0, 3.0), (2.5, 1.0), (4.0, 7.0)]):
+        direc = np.sin(a * np.pi * u) * np.cos(b * u) * (1 - u * u)
+        h = 1e-3
+        Ep = O.window_loss(O.make_plan(d, M, 2.0, m, window="table", table=tab_np + h * direc), fh, x, y)
+        Em = O.window_loss(O.make_plan(d, M, 2.0, m, window="table", table=tab_np - h * direc), fh, x, y)
+        fd = (Ep - Em) / (2 * h)
+        got = float(np.dot(grad, direc))
+        assert abs(got - fd) <= 2e-2 * abs(fd) + 1e-3 * E, (k, got, fd)
+
+
+def test_training_gains_over_sinh_window():
+    """A short training at d = 2, M = 64, m = 3 lowers the held-out error
+    against the trigonometric sum below the sinh window's at the same m."""
+    from paper_2502_07155_gb300.learned import WindowTrainer
+    d, M, m = 2, 64, 3
+    L = 2 * M
+    x = W.nodes_feasible(1 << 14, d, m, L, seed=W.SEED_TRAIN)
+    fh = W.fhat_gaussian(M, d, seed=W.SEED_TRAIN, dtype=np.complex64)
+    y = O.ndft(fh, x).astype(np.complex64)
+    tr = WindowTrainer(d, M, m, lr=3e-3)
+    tr.set_data(to_dev(x), to_dev(fh), to_dev(y))
+    hist = tr.train(400, log_every=100)
+    assert hist[-1][1] < hist[0][1]
+    tab = tr.table_host()
+    xh = W.nodes_feasible(1 << 13, d, m, L, seed=W.SEED_HELDOUT)
+    fhh = W.fhat_gaussian(M, d, seed=W.SEED_HELDOUT, dtype=np.complex64)
+    ref = O.ndft(fhh, xh)
+    errs = {}
+    for name, kw in [("learned", dict(window="table", table=tab)), ("sinh", dict(window="sinh"))]:
+        p = nb.Plan(d, M, 2.0, m, precision="f32", **kw)
+        p.set_nodes(to_dev(xh))
+        errs[name] = rel_l2(to_host(p.forward(to_dev(fhh))), ref)
+    assert errs["learned"] < errs["sinh"] / 1.3, errs

@@ -526,3 +526,46 @@ def test_planted_kernel_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O.Plan, "kernel", _mutant_kernel_no_pi)
     res = _pin_results()
     assert not all(res.values()), res
+
+
+# --------------------------------------------------------------------------- learned-window oracle pieces
+
+def test_mlp_backward_finite_differences():
+    params = O.mlp_init()
+    s = np.linspace(0, 1, 37) ** 2
+    up = np.cos(7 * s) + 0.3
+    g = O.mlp_backward(params, s, up)
+    rng = np.random.default_rng(0)
+    for name in ["W1", "b1", "W2", "b2", "W3", "b3"]:
+        d = rng.standard_normal(params[name].shape)
+        h = 1e-6
+        pp = {k: v.copy() for k, v in params.items()}
+        pm = {k: v.copy() for k, v in params.items()}
+        pp[name] += h * d
+        pm[name] -= h * d
+        fd = (np.dot(up, O.mlp_forward(pp, s)) - np.dot(up, O.mlp_forward(pm, s))) / (2 * h)
+        assert abs(np.sum(g[name] * d) - fd) <= 1e-7 * max(1.0, abs(fd)), name
+
+
+def test_learned_table_grad_finite_differences():
+    params = O.mlp_init()
+    n = 64
+    w = np.sin(np.arange(n + 1) * 0.37)
+    g = O.learned_table_grad(params, w, n)
+    d = np.random.default_rng(1).standard_normal(params["W2"].shape)
+    h = 1e-6
+    pp = {k: v.copy() for k, v in params.items()}
+    pm = {k: v.copy() for k, v in params.items()}
+    pp["W2"] += h * d
+    pm["W2"] -= h * d
+    fd = (np.dot(w, O.learned_table(pp, n)) - np.dot(w, O.learned_table(pm, n))) / (2 * h)
+    assert abs(np.sum(g["W2"] * d) - fd) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_window_loss_zero_at_target():
+    p = O.make_plan(1, 32, 2.0, 3)
+    x = W.nodes_feasible(100, 1, 3, 64, dtype=np.float64)
+    fh = W.fhat_gaussian(32, 1, dtype=np.complex128)
+    y = O.forward(p, fh, x)
+    assert O.window_loss(p, fh, x, y) < 1e-28
+    assert O.window_loss(p, fh, x, O.ndft(fh, x)) > 0
