@@ -155,7 +155,10 @@ bool spread_config(const nfftbl_plan_s* p, int& nb, int& sub, size_t& bytes) {
     const int A = tap_array_len(p->m);
     const int cells = static_cast<int>(box_cells(p->geom));
     const size_t limit = static_cast<size_t>(p->smem_optin);
-    auto layout = [&](int nbv, int subv) { return spread_smem_layout<T>(p->d, A, cells, nbv, subv).total; };
+    auto layout = [&](int nbv, int subv) {
+        return (p->d == 2) ? spread2_layout<T>(A, cells, nbv, 8).total
+                           : spread_smem_layout<T>(p->d, A, cells, nbv, subv).total;
+    };
     for (sub = 256; sub >= 32; sub /= 2) {
         bytes = layout(1, sub);
         if (bytes <= limit) break;

@@ -84,6 +84,30 @@ __host__ __device__ __forceinline__ SpreadSmem spread_smem_layout(int d, int A, 
     return L;
 }
 
+// Row length (elements) of spread2_kernel's per-warp node table: 2A window
+// values, the input value (2 elements), the packed first taps (an int in the
+// next element) and one element of padding; with A even every row starts
+// 16-byte aligned and consecutive rows fall on different bank groups.
+template <typename T>
+__host__ __device__ constexpr int spread2_row(int A) {
+    return 2 * A + 4;
+}
+
+// Shared-memory layout of spread2_kernel (d = 2): the fixed-point box, one
+// 32-row node table per warp, a reduction scratch.
+template <typename T>
+__host__ __device__ __forceinline__ SpreadSmem spread2_layout(int A, int box_cells, int nb, int nwarps) {
+    auto al = [](size_t v) { return (v + 15) / 16 * 16; };
+    SpreadSmem L{};
+    const size_t slot = static_cast<size_t>((box_cells + 1) / 2 * 2);
+    L.box = 0;
+    L.w = al(L.box + static_cast<size_t>(nb) * slot * 16);
+    L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread2_row<T>(A) * sizeof(T));
+    L.lb = L.g = L.run = L.red;
+    L.total = al(L.red + 34 * 8);
+    return L;
+}
+
 // Length of the per-dimension tap arrays of the short-sum kernels: 2m for
 // the compile-time truncations (NFFTBL_FIXED_M_LIST), 24 for the kernel that
 // takes m at run time.

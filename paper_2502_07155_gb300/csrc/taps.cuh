@@ -29,8 +29,18 @@ namespace nfftbl {
 constexpr int kTapThreads = 256;
 constexpr double kPiD = 3.14159265358979323846;
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <typename T> struct FM;
 template <> struct FM<float> {
+    // window arithmetic of the FP32 path: hardware 2^x and reciprocal square
+    // root (a few ulp; the kernels' FP32 accumulation dominates the error)
+    __device__ static float exp2w(float x) { return ex2_approx(x); }
+    __device__ static float sqrtw(float x) { return x * rsqrtf(x); }
     __device__ static float sinpi(float x) { return sinpif(x); }
     __device__ static float cospi(float x) { return cospif(x); }
     __device__ static float sqrt(float x) { return sqrtf(x); }
@@ -42,6 +52,8 @@ template <> struct FM<float> {
     __device__ static float flr(float x) { return floorf(x); }
 };
 template <> struct FM<double> {
+    __device__ static double exp2w(double x) { return ::exp2(x); }
+    __device__ static double sqrtw(double x) { return ::sqrt(x); }
     __device__ static double sinpi(double x) { return ::sinpi(x); }
     __device__ static double cospi(double x) { return ::cospi(x); }
     __device__ static double sqrt(double x) { return ::sqrt(x); }
@@ -118,8 +130,8 @@ __device__ __forceinline__ T win_phi(T delta, const WinParams<T>& w) {
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
     // sinh(beta s)/sinh(beta) = (e^{beta(s-1)} - e^{-beta(s+1)}) / (1 - e^{-2 beta})
-    const T sq = FM<T>::sqrt(q);
-    return (FM<T>::exp2(w.c_exp * (sq - T(1))) - FM<T>::exp2(-w.c_exp * (sq + T(1)))) * w.c_norm;
+    const T sq = FM<T>::sqrtw(q);
+    return (FM<T>::exp2w(w.c_exp * (sq - T(1))) - FM<T>::exp2w(-w.c_exp * (sq + T(1)))) * w.c_norm;
 }
 
 // d Phi / d delta; zero where |delta| >= m (the infinite edge derivative of
@@ -130,9 +142,9 @@ __device__ __forceinline__ T win_dphi(T delta, const WinParams<T>& w) {
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
-    const T sq = FM<T>::sqrt(q);
+    const T sq = FM<T>::sqrtw(q);
     const T ds = -r * w.inv_m / sq;
-    return w.beta * (FM<T>::exp2(w.c_exp * (sq - T(1))) + FM<T>::exp2(-w.c_exp * (sq + T(1)))) * w.c_norm * ds;
+    return w.beta * (FM<T>::exp2w(w.c_exp * (sq - T(1))) + FM<T>::exp2w(-w.c_exp * (sq + T(1)))) * w.c_norm * ds;
 }
 
 // Tap count per dimension: W = 2m fixed at compile time, or W = 0 for a
@@ -198,6 +210,36 @@ __device__ __forceinline__ void tap_weights_d(T tau, T Lt, const WinParams<T>& w
             w[a] = win_phi(delta, wp);
             dw[a] = Lt * win_dphi(delta, wp);
         }
+    }
+}
+
+// Copy a row of A tap weights from shared memory into registers with the
+// widest aligned vector loads the row length allows (rows start 16-byte
+// aligned when A is a multiple of 4 floats / 2 doubles, 8-byte aligned when
+// A is even).
+template <typename T, int A>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&dst)[A]) {
+    if (sizeof(T) == 4 && A % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < A; q += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(src + q);
+            dst[q] = v.x; dst[q + 1] = v.y; dst[q + 2] = v.z; dst[q + 3] = v.w;
+        }
+    } else if (sizeof(T) == 4 && A % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < A; q += 2) {
+            const float2 v = *reinterpret_cast<const float2*>(src + q);
+            dst[q] = v.x; dst[q + 1] = v.y;
+        }
+    } else if (sizeof(T) == 8 && A % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < A; q += 2) {
+            const double2 v = *reinterpret_cast<const double2*>(src + q);
+            dst[q] = v.x; dst[q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < A; ++q) dst[q] = src[q];
     }
 }
 
@@ -524,8 +566,6 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
     const int c = lane % nw;                     // owned contiguous-dimension tap
     const int rg = lane / nw;                    // row group
     const bool active = rg < G;
-    constexpr int RPL = W ? (W + (32 / (W ? W : 1)) - 1) / (32 / (W ? W : 1)) : 24;   // rows per lane (bound)
-    const int rpl = (nw + G - 1) / G;
 
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
@@ -582,10 +622,21 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
                             s_g[bb * sub + tid] = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
                     }
                     __syncthreads();
-                    // ---- runs of nodes in one cell (block-wide compaction of run starts)
+                    // ---- groups of consecutive (cell-sorted) nodes: for d = 1 the nodes of
+                    // one cell; for d >= 2 the nodes of one box row (same leading taps)
+                    // whose contiguous-dimension first tap lies in one segment of S cells,
+                    // so that the group's taps span at most 32 columns (one per lane)
+                    const int S = 33 - nw;
                     int nruns = 0;
                     {
-                        const int flag = (tid < ns) && (tid == 0 || s_lb[tid] != s_lb[tid - 1]);
+                        auto key = [&](int j) -> int {
+                            const int lbp = s_lb[j];
+                            if (D != 2) return lbp;
+                            const int fast = (D == 2) ? ((lbp >> 10) & 1023) : (lbp >> 20);
+                            const int lead = (D == 2) ? (lbp & 1023) : (lbp & 0xFFFFF);
+                            return lead | ((fast / S) << 20);
+                        };
+                        const int flag = (tid < ns) && (tid == 0 || key(tid) != key(tid - 1));
                         const unsigned bal = __ballot_sync(0xffffffffu, flag);
                         const int before = __popc(bal & ((1u << lane) - 1u));
                         if (lane == 0) s_red[warp] = __popc(bal);
@@ -597,17 +648,15 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
                         if (tid == 0) s_run[nruns] = ns;
                         __syncthreads();
                     }
-                    // ---- accumulate runs
-                    if (active) {
-                        for (int r = warp; r < nruns; r += nwarps) {
-                            const int jlo = s_run[r], jhi = s_run[r + 1];
-                            const int lbp = s_lb[jlo];
-                            const int lb0 = lbp & 1023, lb1 = (lbp >> 10) & 1023, lb2 = lbp >> 20;
-                            for (int bb = 0; bb < nb; ++bb) {
-                                U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
-                                const CT* gg = s_g + bb * sub;
-                                if (D == 1) {
-                                    // row groups split the run's nodes; sums are exact in fixed point
+                    if (D == 1) {
+                        // lanes own taps; row groups split the run's nodes (sums are exact)
+                        if (active) {
+                            for (int r = warp; r < nruns; r += nwarps) {
+                                const int jlo = s_run[r], jhi = s_run[r + 1];
+                                const int lb0 = s_lb[jlo] & 1023;
+                                for (int bb = 0; bb < nb; ++bb) {
+                                    U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
+                                    const CT* gg = s_g + bb * sub;
                                     T ar = T(0), ai = T(0);
                                     for (int j = jlo + rg; j < jhi; j += G) {
                                         const T wv = s_w[static_cast<size_t>(j) * A + c];
@@ -617,60 +666,86 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
                                     const int cell = lb0 + c;
                                     fixed_add(bx + 2 * cell, to_fixed<T>(ar, inv_q));
                                     fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai, inv_q));
-                                } else if (D == 2) {
-                                    T ar[RPL], ai[RPL];
+                                }
+                            }
+                        }
+                    } else {
+                        // lanes own absolute box columns; each sums its column's
+                        // contributions over the group for all 2m rows in registers
+                        for (int r = warp; r < nruns; r += nwarps) {
+                            const int jlo = s_run[r], jhi = s_run[r + 1];
+                            const int lbp = s_lb[jlo];
+                            const int lb0 = lbp & 1023, lb1 = (lbp >> 10) & 1023;
+                            const int fast0 = (((D == 2) ? lb1 : (lbp >> 20)) / S) * S;
+                            const int col = fast0 + lane;
+                            const bool live = col < a.g.box[D - 1];
+                            for (int bb = 0; bb < nb; ++bb) {
+                                U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
+                                const CT* gg = s_g + bb * sub;
+                                if (D == 2) {
+                                    T ar[A], ai[A];
 #pragma unroll
-                                    for (int k = 0; k < RPL; ++k) ar[k] = ai[k] = T(0);
+                                    for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
                                     for (int j = jlo; j < jhi; ++j) {
                                         const T* wj = s_w + static_cast<size_t>(j) * 2 * A;
-                                        const T wf = wj[A + c];
-                                        const T gr = gg[j].x * wf, gi = gg[j].y * wf;
+                                        const int t = col - ((s_lb[j] >> 10) & 1023);
+                                        const bool in = (t >= 0) && (t < nw);
+                                        const T wf = in ? wj[A + (in ? t : 0)] : T(0);
+                                        const CT gv = gg[j];
+                                        const T gr = gv.x * wf, gi = gv.y * wf;
+                                        T w0r[A];
+                                        load_row<T, A>(wj, w0r);
 #pragma unroll
-                                        for (int k = 0; k < RPL; ++k) {
-                                            const int row = rg + G * k;
-                                            if (k < rpl && row < nw) {
-                                                ar[k] += gr * wj[row];
-                                                ai[k] += gi * wj[row];
+                                        for (int q = 0; q < A; ++q) {
+                                            if (q < nw) {
+                                                ar[q] += gr * w0r[q];
+                                                ai[q] += gi * w0r[q];
                                             }
                                         }
                                     }
-                                    const int pitch = a.g.box[1];
+                                    if (live) {
+                                        const int pitch = a.g.box[1];
 #pragma unroll
-                                    for (int k = 0; k < RPL; ++k) {
-                                        const int row = rg + G * k;
-                                        if (k < rpl && row < nw) {
-                                            const int cell = (lb0 + row) * pitch + lb1 + c;
-                                            fixed_add(bx + 2 * cell, to_fixed<T>(ar[k], inv_q));
-                                            fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[k], inv_q));
+                                        for (int q = 0; q < A; ++q) {
+                                            if (q < nw) {
+                                                const int cell = (lb0 + q) * pitch + col;
+                                                fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
+                                                fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
+                                            }
                                         }
                                     }
                                 } else {
                                     const int p2 = a.g.box[2];
                                     const int p1 = a.g.box[1] * p2;
                                     for (int a0 = 0; a0 < nw; ++a0) {
-                                        T ar[RPL], ai[RPL];
+                                        T ar[A], ai[A];
 #pragma unroll
-                                        for (int k = 0; k < RPL; ++k) ar[k] = ai[k] = T(0);
+                                        for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
                                         for (int j = jlo; j < jhi; ++j) {
                                             const T* wj = s_w + static_cast<size_t>(j) * 3 * A;
-                                            const T wf = wj[2 * A + c] * wj[a0];
-                                            const T gr = gg[j].x * wf, gi = gg[j].y * wf;
+                                            const int t = col - (s_lb[j] >> 20);
+                                            const bool in = (t >= 0) && (t < nw);
+                                            const T wf = in ? wj[2 * A + (in ? t : 0)] * wj[a0] : T(0);
+                                            const CT gv = gg[j];
+                                            const T gr = gv.x * wf, gi = gv.y * wf;
+                                            T w1r[A];
+                                            load_row<T, A>(wj + A, w1r);
 #pragma unroll
-                                            for (int k = 0; k < RPL; ++k) {
-                                                const int row = rg + G * k;
-                                                if (k < rpl && row < nw) {
-                                                    ar[k] += gr * wj[A + row];
-                                                    ai[k] += gi * wj[A + row];
+                                            for (int q = 0; q < A; ++q) {
+                                                if (q < nw) {
+                                                    ar[q] += gr * w1r[q];
+                                                    ai[q] += gi * w1r[q];
                                                 }
                                             }
                                         }
+                                        if (live) {
 #pragma unroll
-                                        for (int k = 0; k < RPL; ++k) {
-                                            const int row = rg + G * k;
-                                            if (k < rpl && row < nw) {
-                                                const int cell = (lb0 + a0) * p1 + (lb1 + row) * p2 + lb2 + c;
-                                                fixed_add(bx + 2 * cell, to_fixed<T>(ar[k], inv_q));
-                                                fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[k], inv_q));
+                                            for (int q = 0; q < A; ++q) {
+                                                if (q < nw) {
+                                                    const int cell = (lb0 + a0) * p1 + (lb1 + q) * p2 + col;
+                                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
+                                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
+                                                }
                                             }
                                         }
                                     }
@@ -682,6 +757,163 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
                 }
             }
             // ---- store the item's box (plan precision) to its scratch slot
+            for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
+                const int bb = idx / box_cells;
+                const int cell = idx - bb * box_cells;
+                const U* u = boxu + (static_cast<size_t>(bb) * slot + cell) * 2;
+                CT v;
+                v.x = static_cast<T>(static_cast<double>(static_cast<long long>(u[0])) * qd);
+                v.y = static_cast<T>(static_cast<double>(static_cast<long long>(u[1])) * qd);
+                a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// d = 2 spreading without block barriers inside a work item: warp w walks a
+// contiguous share of the item's (cell-sorted) nodes in chunks of 32.
+//  Phase A: lane l evaluates the 2 x 2m window values of chunk node l (one
+//    node per lane, fully unrolled) into row l of the warp's shared-memory
+//    node table, with the node's input value and first taps.
+//  Phase B: the warp walks the chunk's rows in order.  Lanes own absolute
+//    box columns; consecutive nodes of one box row whose contiguous-
+//    dimension first tap lies in one segment of S = 33 - 2m cells share the
+//    lanes' register accumulators (2m rows per lane), which go to the
+//    64-bit fixed-point box (exact integer adds) when the segment changes.
+// Shares of different warps may meet in a cell; their fixed-point sums add
+// exactly, so the result does not depend on timing.
+template <typename T, int W>
+__global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_kernel(const TapArgs<T> a) {
+    using CT = C2<T>;
+    using U = unsigned long long;
+    constexpr int A = TapN<W>::A;
+    constexpr int RS = spread2_row<T>(A);   // node-table row: w0[A] | w1[A] | g.x g.y lb pad
+    static_assert(A % 2 == 0, "node-table rows must stay 16-byte aligned");
+    const int nw = W ? W : 2 * a.w.m;
+    const int m = nw / 2;
+    const int S = 33 - nw;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int box1 = a.g.box[1];
+    const int box_cells = a.g.box[0] * box1;
+    const int slot = (box_cells + 1) / 2 * 2;
+    const int nbmax = a.spread_batch;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const SpreadSmem Ls = spread2_layout<T>(A, box_cells, nbmax, nwarps);
+    U* boxu = reinterpret_cast<U*>(smem + Ls.box);
+    T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
+    double* s_red = reinterpret_cast<double*>(smem + Ls.red);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+        const WorkItem wi = a.work[item];
+        int org[3] = {0, 0, 0};
+        tile_origin<2>(a.g, wi.tile, periodic, org);
+        for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
+            const int nb = min(nbmax, a.batch - b0);
+            double part = 0.0;
+            for (int j = tid; j < wi.count; j += blockDim.x) {
+                const long long src = a.perm[wi.start + j];
+                for (int bb = 0; bb < nb; ++bb) {
+                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
+                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+            if (lane == 0) s_red[warp] = part;
+            for (int idx = tid; idx < nb * slot * 2; idx += blockDim.x) boxu[idx] = 0ull;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+                tot *= static_cast<double>(a.wbound) * 1.0001;
+                int e = 0;
+                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e; 2^(62-e) stays a finite float
+                s_red[32] = ldexp(1.0, e - 62);                // quantum q
+                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            const double qd = s_red[32];
+            const T inv_q = static_cast<T>(1.0 / qd);
+            if (s_red[33] != 0.0) {
+                const int per = (wi.count + nwarps - 1) / nwarps;
+                const int jlo = warp * per, jhi = min(wi.count, jlo + per);
+                for (int bb = 0; bb < nb; ++bb) {
+                    U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
+                    int seg = -1, seg_lb0 = 0, col = 0;
+                    T ar[A], ai[A];
+#pragma unroll
+                    for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                    auto flush = [&]() {
+                        if (col < box1) {
+#pragma unroll
+                            for (int q = 0; q < A; ++q) {
+                                if (q < nw) {
+                                    const int cell = (seg_lb0 + q) * box1 + col;
+                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
+                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
+                                }
+                            }
+                        }
+                    };
+                    for (int c0 = jlo; c0 < jhi; c0 += 32) {
+                        const int nc = min(32, jhi - c0);
+                        // ---- phase A: this lane's node
+                        if (lane < nc) {
+                            const long long i = static_cast<long long>(wi.start) + c0 + lane;
+                            T tau[3];
+                            int lb[3] = {0, 0, 0};
+                            node_setup<T, 2>(a.xs, i, a.g, org, tau, lb, m);
+                            T* row = s_tab + lane * RS;
+                            T wt[A];
+                            tap_weights<T, W>(tau[0], a.w, wt);
+#pragma unroll
+                            for (int q = 0; q < A; ++q)
+                                if (q < nw) row[q] = wt[q];
+                            tap_weights<T, W>(tau[1], a.w, wt);
+#pragma unroll
+                            for (int q = 0; q < A; ++q)
+                                if (q < nw) row[A + q] = wt[q];
+                            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
+                            row[2 * A] = gv.x;
+                            row[2 * A + 1] = gv.y;
+                            reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
+                        }
+                        __syncwarp();
+                        // ---- phase B: walk the chunk
+#pragma unroll 1
+                        for (int k = 0; k < nc; ++k) {
+                            const T* row = s_tab + k * RS;
+                            const int lbk = reinterpret_cast<const int*>(row + 2 * A + 2)[0];
+                            const int lb0 = lbk & 0xFFFF, lb1 = lbk >> 16;
+                            const int key = lb0 | ((lb1 / S) << 16);
+                            if (key != seg) {
+                                if (seg >= 0) flush();
+                                seg = key;
+                                seg_lb0 = lb0;
+                                col = (lb1 / S) * S + lane;
+#pragma unroll
+                                for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                            }
+                            const int t = col - lb1;
+                            const bool in = (t >= 0) && (t < nw);
+                            const T wf = in ? row[A + (in ? t : 0)] : T(0);
+                            const T gr = row[2 * A] * wf, gi = row[2 * A + 1] * wf;
+                            T w0r[A];
+                            load_row<T, A>(row, w0r);
+#pragma unroll
+                            for (int q = 0; q < A; ++q) {
+                                if (q < nw) {
+                                    ar[q] += gr * w0r[q];
+                                    ai[q] += gi * w0r[q];
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (seg >= 0) flush();
+                }
+            }
+            __syncthreads();
             for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
                 const int bb = idx / box_cells;
                 const int cell = idx - bb * box_cells;
@@ -849,7 +1081,8 @@ template <typename T, int D, int W>
 nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem) {
     void* fn = nullptr;
     if (kind == TAP_INTERP) fn = reinterpret_cast<void*>(interp_kernel<T, D, W>);
-    if (kind == TAP_SPREAD) fn = reinterpret_cast<void*>(spread_kernel<T, D, W>);
+    if (kind == TAP_SPREAD)
+        fn = (D == 2) ? reinterpret_cast<void*>(spread2_kernel<T, W>) : reinterpret_cast<void*>(spread_kernel<T, D, W>);
     if (kind == TAP_GRAD) fn = reinterpret_cast<void*>(node_grad_kernel<T, D, W>);
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           static_cast<int>(smem)),
@@ -866,6 +1099,8 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     timing_begin(p, kind == TAP_INTERP ? NFFTBL_K_INTERP : kind == TAP_SPREAD ? NFFTBL_K_SPREAD : NFFTBL_K_GRAD);
     if (kind == TAP_INTERP)
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
+    else if (kind == TAP_SPREAD && D == 2)
+        spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
     else if (kind == TAP_SPREAD)
         spread_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(args);
     else

@@ -75,9 +75,15 @@ def test_mlp_backward_matches_oracle(kind, tol_bf16):
     got = params_to_dict(to_host(grad))
     ref = O.learned_table_grad(params_to_dict(pf), dEdv, n)
     scale = np.sqrt(sum(np.sum(v ** 2) for v in ref.values()))
+    # d/db3 is exactly zero (b3 cancels in g(u^2) - g(0)); the kernel's value is
+    # what is left of FP32 sums over the n + 1 points, bounded to first order
+    # by recursive summation: (n + 1) 2^-24 sum_i |dE/dv_i v_i|
+    b3_bound = (n + 1) * 2.0 ** -24 * np.sum(np.abs(dEdv * O.learned_table(params_to_dict(pf))))
+    assert abs(float(got["b3"].reshape(-1)[0])) <= b3_bound
     for name in ref:
+        if name == "b3":
+            continue
         tol = tol_bf16 if name in ("W1", "b1", "W2") else 1e-4   # BF16 products feed W1, b1, W2
-        # d/db3 is exactly zero (b3 cancels in g(u^2) - g(0)): normalise by the full gradient
         err = np.linalg.norm(got[name].reshape(-1) - ref[name].reshape(-1))
         assert err < tol * max(np.linalg.norm(ref[name]), 1e-3 * scale), name
 
