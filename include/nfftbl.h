@@ -86,7 +86,7 @@ typedef struct {
                                u_i = i/(table_len-1), i = 0..table_len-1, copied by the plan */
     int table_len;          /* >= 3 for NFFTBL_WIN_TABLE                                  */
     int tile[3];            /* node-binning tile shape in grid cells; 0 = default         */
-    int nodes_per_item;     /* nodes per (tile, chunk) work item; 0 = default             */
+    int nodes_per_item;     /* nodes per (tile, chunk) work item, <= 2047; 0 = default 1024 */
 } nfftbl_opts;
 
 /* Fill *opts with the defaults listed above. */

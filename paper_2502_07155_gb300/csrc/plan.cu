@@ -155,9 +155,11 @@ bool spread_config(const nfftbl_plan_s* p, int& nb, int& sub, size_t& bytes) {
     const int A = tap_array_len(p->m);
     const int cells = static_cast<int>(box_cells(p->geom));
     const size_t limit = static_cast<size_t>(p->smem_optin);
+    const int w3 = spread3_warps<T>(A, cells, limit);
     auto layout = [&](int nbv, int subv) {
-        return (p->d == 2) ? spread2_layout<T>(A, cells, nbv, 8).total
-                           : spread_smem_layout<T>(p->d, A, cells, nbv, subv).total;
+        if (p->d == 2) return spread2_layout<T>(A, cells, nbv, 8).total;
+        if (p->d == 3) return spread3_layout<T>(A, cells, nbv, w3).total;
+        return spread_smem_layout<T>(p->d, A, cells, nbv, subv).total;
     };
     for (sub = 256; sub >= 32; sub /= 2) {
         bytes = layout(1, sub);
@@ -199,6 +201,8 @@ nfftbl_status run_taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, 
             return fail(p, NFFTBL_EUNSUPPORTED, "spread box does not fit in shared memory");
         a.spread_batch = nb;
         a.spread_sub = sub;
+        a.spread_warps = spread3_warps<T>(tap_array_len(p->m), static_cast<int>(box_cells(p->geom)),
+                                          static_cast<size_t>(p->smem_optin));
     }
     switch (p->d) {
         case 1: return run_taps_d<T, 1>(p, a, kind, smem);
@@ -355,7 +359,8 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     if (o.batch < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "batch must be >= 1");
     if (window == NFFTBL_WIN_TABLE && (!o.table || o.table_len < 3))
         return plan_fail(nullptr, NFFTBL_EINVAL, "table window needs a table of >= 3 values");
-    if (o.nodes_per_item < 0) return plan_fail(nullptr, NFFTBL_EINVAL, "nodes_per_item must be >= 0");
+    if (o.nodes_per_item < 0 || o.nodes_per_item > 2047)
+        return plan_fail(nullptr, NFFTBL_EINVAL, "nodes_per_item must be in [0, 2047]");
     int L[3] = {1, 1, 1};
     for (int t = 0; t < d; ++t) {
         if (M[t] < 2 || (M[t] & 1)) return plan_fail(nullptr, NFFTBL_EINVAL, "each M_t must be even and >= 2");
@@ -401,8 +406,8 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
         const bool tma_ok = 2 * g.box[d - 1] <= 256 && (d < 2 || g.box[0] <= 256) && (d < 3 || g.box[1] <= 256);
         const int bc = static_cast<int>(box_cells(g));
         const int A = tap_array_len(m);
-        const size_t spread_min = (o.precision == NFFTBL_F64) ? spread_smem_layout<double>(d, A, bc, 1, 32).total
-                                                              : spread_smem_layout<float>(d, A, bc, 1, 32).total;
+        const size_t spread_min = (o.precision == NFFTBL_F64) ? spread_min_smem<double>(d, A, bc, optin)
+                                                              : spread_min_smem<float>(d, A, bc, optin);
         if (bytes <= kBoxMax && tma_ok && spread_min <= static_cast<size_t>(optin)) break;
         if (user_tile) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "tile box exceeds shared memory or TMA limits");
         int big = 0;

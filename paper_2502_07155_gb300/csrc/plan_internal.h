@@ -62,6 +62,7 @@ struct TapArgs {
     int spread_sub;            // nodes staged per pass in shared memory
     int spread_batch;          // batch entries per shared-memory box group
     T wbound;                  // bound on prod_t |window factor| (1 for sinh / cKB)
+    int spread_warps;          // warps per block of the d = 3 spread kernel
 };
 
 // Shared-memory layout of spread_kernel (byte offsets), shared with the host.
@@ -106,6 +107,41 @@ __host__ __device__ __forceinline__ SpreadSmem spread2_layout(int A, int box_cel
     L.lb = L.g = L.run = L.red;
     L.total = al(L.red + 34 * 8);
     return L;
+}
+
+// Shared-memory layout of spread3_kernel (d = 3): the fixed-point box (16
+// bytes per cell), one 32-row node table per warp (rows of 3A window values,
+// the input value, the packed first taps and padding), a reduction scratch.
+template <typename T>
+__host__ __device__ constexpr int spread3_row(int A) {
+    return 3 * A + 4;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ SpreadSmem spread3_layout(int A, int box_cells, int nb, int nwarps) {
+    auto al = [](size_t v) { return (v + 15) / 16 * 16; };
+    SpreadSmem L{};
+    L.box = 0;
+    L.w = al(L.box + static_cast<size_t>(nb) * box_cells * 16);
+    L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread3_row<T>(A) * sizeof(T));
+    L.lb = L.g = L.run = L.red;
+    L.total = al(L.red + 34 * 8);
+    return L;
+}
+
+// Warps per block of spread3_kernel: 16 in FP32 when the tables fit, else 8.
+template <typename T>
+__host__ __forceinline__ int spread3_warps(int A, int box_cells, size_t limit) {
+    if (sizeof(T) == 4 && spread3_layout<T>(A, box_cells, 1, 16).total <= limit) return 16;
+    return 8;
+}
+
+// Shared memory of the spread kernel for dimension d (minimum batch group).
+template <typename T>
+__host__ __forceinline__ size_t spread_min_smem(int d, int A, int box_cells, size_t limit) {
+    if (d == 2) return spread2_layout<T>(A, box_cells, 1, 8).total;
+    if (d == 3) return spread3_layout<T>(A, box_cells, 1, spread3_warps<T>(A, box_cells, limit)).total;
+    return spread_smem_layout<T>(d, A, box_cells, 1, 32).total;
 }
 
 // Length of the per-dimension tap arrays of the short-sum kernels: 2m for

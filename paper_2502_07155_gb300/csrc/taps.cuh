@@ -928,6 +928,195 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
     }
 }
 
+// Fixed-point cells of the d = 3 spreading box (16 bytes per cell).
+//  FP32: each component holds v = hi * 2^21 + lo in two int32 words, with
+//    the quantum chosen so that the item's total stays below 2^42 quanta.  A
+//    value X (in quanta, |X| < 2^42) splits exactly with float arithmetic:
+//    hi = rint(X 2^-21) and lo = rint(X - hi 2^21), |lo| <= 2^20, both read
+//    off the bits of y + 1.5 * 2^23 (valid for |y| < 2^22).  An item adds at
+//    most 2047 times to a cell, so neither word can overflow, and integer
+//    addition keeps the sum exact and independent of order.  32-bit shared
+//    atomics are several times faster than 64-bit ones.
+//  FP64: one 64-bit word per component, total below 2^62 quanta.
+template <typename T> struct Fixed3;
+template <> struct Fixed3<float> {
+    static constexpr int kBits = 42;
+    __device__ static void add(unsigned char* cell, float xr, float xi) {
+        int* w = reinterpret_cast<int*>(cell);
+        split(w, xr);
+        split(w + 2, xi);
+    }
+    __device__ static void split(int* w, float X) {
+        const float magic = 12582912.0f;   // 1.5 * 2^23
+        const float h = fmaf(X, 0x1p-21f, magic);
+        const int hi = __float_as_int(h) - 0x4B400000;
+        const float lo_f = fmaf(-(h - magic), 0x1p21f, X);
+        const int lo = __float_as_int(lo_f + magic) - 0x4B400000;
+        if (hi != 0) atomicAdd(w, hi);
+        if (lo != 0) atomicAdd(w + 1, lo);
+    }
+    __device__ static double value(const unsigned char* cell, int comp) {
+        const int* w = reinterpret_cast<const int*>(cell) + 2 * comp;
+        return static_cast<double>(static_cast<long long>(w[0]) * (1ll << 21) + static_cast<long long>(w[1]));
+    }
+};
+template <> struct Fixed3<double> {
+    static constexpr int kBits = 62;
+    __device__ static void add(unsigned char* cell, double xr, double xi) {
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(cell);
+        const long long vr = __double2ll_rn(xr), vi = __double2ll_rn(xi);
+        if (vr != 0) atomicAdd(w, static_cast<unsigned long long>(vr));
+        if (vi != 0) atomicAdd(w + 1, static_cast<unsigned long long>(vi));
+    }
+    __device__ static double value(const unsigned char* cell, int comp) {
+        return static_cast<double>(reinterpret_cast<const long long*>(cell)[comp]);
+    }
+};
+
+// d = 3 spreading.  Warp w walks a contiguous share of the item's (cell-
+// sorted) nodes in chunks of 32: lane l first evaluates the 3 x 2m window
+// values of chunk node l into row l of the warp's node table (the input
+// value is stored pre-scaled to quanta); the warp then takes the chunk's
+// runs of nodes with equal first taps (same cell).  For a run, lane l owns
+// the (a1, a2) tap pairs l, l + 32, ... of the (2m)^2 pairs and sums, over
+// the run's nodes, the 2m values of its pair along dimension 0 in
+// registers; each sum goes to the box once.
+template <typename T, int W>
+__global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
+    using CT = C2<T>;
+    constexpr int A = TapN<W>::A;
+    constexpr int RS = spread3_row<T>(A);
+    static_assert(A % 2 == 0, "node-table rows must stay 16-byte aligned");
+    const int nw = W ? W : 2 * a.w.m;
+    const int m = nw / 2;
+    const int npairs = nw * nw;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int bx0 = a.g.box[0], bx1 = a.g.box[1], bx2 = a.g.box[2];
+    const int box_cells = bx0 * bx1 * bx2;
+    const int nbmax = a.spread_batch;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const SpreadSmem Ls = spread3_layout<T>(A, box_cells, nbmax, nwarps);
+    unsigned char* boxc = smem + Ls.box;
+    unsigned long long* boxz = reinterpret_cast<unsigned long long*>(smem + Ls.box);
+    T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
+    double* s_red = reinterpret_cast<double*>(smem + Ls.red);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+        const WorkItem wi = a.work[item];
+        int org[3] = {0, 0, 0};
+        tile_origin<3>(a.g, wi.tile, periodic, org);
+        for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
+            const int nb = min(nbmax, a.batch - b0);
+            double part = 0.0;
+            for (int j = tid; j < wi.count; j += blockDim.x) {
+                const long long src = a.perm[wi.start + j];
+                for (int bb = 0; bb < nb; ++bb) {
+                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
+                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+            if (lane == 0) s_red[warp] = part;
+            for (int idx = tid; idx < nb * box_cells * 2; idx += blockDim.x) boxz[idx] = 0ull;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+                tot *= static_cast<double>(a.wbound) * 1.0001;
+                int e = 0;
+                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e
+                s_red[32] = ldexp(1.0, e - Fixed3<T>::kBits);   // quantum q
+                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            const double qd = s_red[32];
+            const T inv_q = static_cast<T>(1.0 / qd);
+            if (s_red[33] != 0.0) {
+                const int per = (wi.count + nwarps - 1) / nwarps;
+                const int jlo = warp * per, jhi = min(wi.count, jlo + per);
+                for (int bb = 0; bb < nb; ++bb) {
+                    unsigned char* bx = boxc + static_cast<size_t>(bb) * box_cells * 16;
+                    for (int c0 = jlo; c0 < jhi; c0 += 32) {
+                        const int nc = min(32, jhi - c0);
+                        // ---- phase A: this lane's node
+                        if (lane < nc) {
+                            const long long i = static_cast<long long>(wi.start) + c0 + lane;
+                            T tau[3];
+                            int lb[3] = {0, 0, 0};
+                            node_setup<T, 3>(a.xs, i, a.g, org, tau, lb, m);
+                            T* row = s_tab + lane * RS;
+                            T wt[A];
+#pragma unroll
+                            for (int t = 0; t < 3; ++t) {
+                                tap_weights<T, W>(tau[t], a.w, wt);
+#pragma unroll
+                                for (int q = 0; q < A; ++q)
+                                    if (q < nw) row[t * A + q] = wt[q];
+                            }
+                            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
+                            row[3 * A] = gv.x * inv_q;
+                            row[3 * A + 1] = gv.y * inv_q;
+                            reinterpret_cast<int*>(row + 3 * A + 2)[0] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
+                        }
+                        __syncwarp();
+                        // ---- phase B: runs of equal first taps
+                        int k = 0;
+                        while (k < nc) {
+                            const int key = reinterpret_cast<const int*>(s_tab + k * RS + 3 * A + 2)[0];
+                            int k1 = k + 1;
+                            while (k1 < nc && reinterpret_cast<const int*>(s_tab + k1 * RS + 3 * A + 2)[0] == key) ++k1;
+                            const int lb0 = key & 1023, lb1 = (key >> 10) & 1023, lb2 = key >> 20;
+                            for (int p0 = 0; p0 < npairs; p0 += 32) {
+                                const int pp = p0 + lane;
+                                const bool valid = pp < npairs;
+                                const int a1 = valid ? pp / nw : 0;
+                                const int a2 = valid ? pp - a1 * nw : 0;
+                                T ar[A], ai[A];
+#pragma unroll
+                                for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                                for (int kk = k; kk < k1; ++kk) {
+                                    const T* row = s_tab + kk * RS;
+                                    const T w12 = row[A + a1] * row[2 * A + a2];
+                                    const T gr = row[3 * A] * w12, gi = row[3 * A + 1] * w12;
+                                    T w0r[A];
+                                    load_row<T, A>(row, w0r);
+#pragma unroll
+                                    for (int q = 0; q < A; ++q) {
+                                        if (q < nw) {
+                                            ar[q] += gr * w0r[q];
+                                            ai[q] += gi * w0r[q];
+                                        }
+                                    }
+                                }
+                                if (valid) {
+                                    const int base = (lb0 * bx1 + lb1 + a1) * bx2 + lb2 + a2;
+                                    const int pitch0 = bx1 * bx2;
+#pragma unroll
+                                    for (int q = 0; q < A; ++q)
+                                        if (q < nw) Fixed3<T>::add(bx + static_cast<size_t>(base + q * pitch0) * 16, ar[q], ai[q]);
+                                }
+                            }
+                            k = k1;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
+                const int bb = idx / box_cells;
+                const int cell = idx - bb * box_cells;
+                const unsigned char* c = boxc + (static_cast<size_t>(bb) * box_cells + cell) * 16;
+                CT v;
+                v.x = static_cast<T>(Fixed3<T>::value(c, 0) * qd);
+                v.y = static_cast<T>(Fixed3<T>::value(c, 1) * qd);
+                a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Ordered flush: grid[b][l] = sum over the boxes covering l, in a fixed order.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) gather_kernel(const TapArgs<T> a) {
@@ -1082,14 +1271,17 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     void* fn = nullptr;
     if (kind == TAP_INTERP) fn = reinterpret_cast<void*>(interp_kernel<T, D, W>);
     if (kind == TAP_SPREAD)
-        fn = (D == 2) ? reinterpret_cast<void*>(spread2_kernel<T, W>) : reinterpret_cast<void*>(spread_kernel<T, D, W>);
+        fn = (D == 2)   ? reinterpret_cast<void*>(spread2_kernel<T, W>)
+             : (D == 3) ? reinterpret_cast<void*>(spread3_kernel<T, W>)
+                        : reinterpret_cast<void*>(spread_kernel<T, D, W>);
+    const int threads = (kind == TAP_SPREAD && D == 3) ? 32 * args.spread_warps : kTapThreads;
     if (kind == TAP_GRAD) fn = reinterpret_cast<void*>(node_grad_kernel<T, D, W>);
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           static_cast<int>(smem)),
                                   "tap smem attribute");
     if (st != NFFTBL_OK) return st;
     int occ = 0;
-    st = check_cuda(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTapThreads, smem), "occupancy");
+    st = check_cuda(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem), "occupancy");
     if (st != NFFTBL_OK) return st;
     if (occ < 1) return fail(p, NFFTBL_EUNSUPPORTED, "tap kernel does not fit on an SM");
     const long long want = static_cast<long long>(occ) * p->num_sms;
@@ -1101,6 +1293,8 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
     else if (kind == TAP_SPREAD && D == 2)
         spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
+    else if (kind == TAP_SPREAD && D == 3)
+        spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
     else if (kind == TAP_SPREAD)
         spread_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(args);
     else
