@@ -105,7 +105,7 @@ __host__ __device__ __forceinline__ SpreadSmem spread2_layout(int A, int box_cel
     L.w = al(L.box + static_cast<size_t>(nb) * slot * 16);
     L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread2_row<T>(A) * sizeof(T));
     L.lb = L.g = L.run = L.red;
-    L.total = al(L.red + 34 * 8);
+    L.total = al(L.red + 40 * 8);
     return L;
 }
 
@@ -125,7 +125,7 @@ __host__ __device__ __forceinline__ SpreadSmem spread3_layout(int A, int box_cel
     L.w = al(L.box + static_cast<size_t>(nb) * box_cells * 16);
     L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread3_row<T>(A) * sizeof(T));
     L.lb = L.g = L.run = L.red;
-    L.total = al(L.red + 34 * 8);
+    L.total = al(L.red + 40 * 8);
     return L;
 }
 

@@ -153,12 +153,37 @@ template <int W> struct TapN {
     static constexpr int A = W ? W : 24;
 };
 
+// One Shannon / sinh tap weight (the FAST case of tap_weights) for tap a;
+// s = sin(pi tau).
+template <typename T>
+__device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
+    const int n = m - 1 - a;
+    const T delta = tau + static_cast<T>(n);
+    const T r = delta * wp.inv_m;
+    const T q = fma(-r, r, T(1));
+    const bool in = q > T(0);
+    const T sq = FM<T>::sqrtw(in ? q : T(1));
+    const T ph = (FM<T>::exp2w(wp.c_exp * (sq - T(1))) - FM<T>::exp2w(-wp.c_exp * (sq + T(1)))) * wp.c_norm;
+    const T num = (n & 1) ? -s : s;
+    const T sc = (delta == T(0)) ? T(1) : FM<T>::div(num, static_cast<T>(kPiD) * delta);
+    return in ? sc * ph : T(0);
+}
+
 // The 2m tap weights psi_t(x - l/L) (Shannon) or phi_t(x - l/L) (classical)
-// of one dimension, tap a at l = i - m + 1 + a.
-template <typename T, int W>
+// of one dimension, tap a at l = i - m + 1 + a.  FAST = true is the
+// Shannon method with the sinh window (the default plan), evaluated inline
+// with no per-tap dispatch; the caller checks that the plan is of that kind.
+template <typename T, int W, bool FAST = false>
 __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w)[TapN<W>::A]) {
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
+    if (FAST) {
+        const T s = FM<T>::sinpi(tau);
+#pragma unroll
+        for (int a = 0; a < TapN<W>::A; ++a)
+            if (a < nw) w[a] = shannon_sinh_weight(tau, s, a, m, wp);
+        return;
+    }
     if (wp.method == NFFTBL_SHANNON) {
         const T s = FM<T>::sinpi(tau);
 #pragma unroll
@@ -172,6 +197,25 @@ __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w
     } else {
 #pragma unroll
         for (int a = 0; a < nw; ++a) w[a] = win_phi(tau + static_cast<T>(m - 1 - a), wp);
+    }
+}
+
+// Write the 2m tap weights of one dimension to dst[0 .. 2m-1] (shared
+// memory), one at a time.
+template <typename T, int W>
+__device__ __forceinline__ void tap_weights_to(T* dst, bool fast, T tau, const WinParams<T>& wp) {
+    const int m = W ? W / 2 : wp.m;
+    const int nw = 2 * m;
+    if (fast) {
+        const T s = FM<T>::sinpi(tau);
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) dst[a] = shannon_sinh_weight(tau, s, a, m, wp);
+    } else {
+        T wt[TapN<W>::A];
+        tap_weights<T, W>(tau, wp, wt);
+#pragma unroll
+        for (int q = 0; q < TapN<W>::A; ++q)
+            if (q < nw) dst[q] = wt[q];
     }
 }
 
@@ -473,6 +517,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
     __syncthreads();
     uint32_t phase = 0;
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
     constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     const int m = nw / 2;
@@ -492,9 +537,15 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 int lb[3] = {0, 0, 0};
                 node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
                 T w0[A], w1[A], w2[A];
-                tap_weights<T, W>(tau[0], a.w, w0);
-                if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
-                if (D > 2) tap_weights<T, W>(tau[2], a.w, w2);
+                if (fast) {
+                    tap_weights<T, W, true>(tau[0], a.w, w0);
+                    if (D > 1) tap_weights<T, W, true>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
+                } else {
+                    tap_weights<T, W>(tau[0], a.w, w0);
+                    if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W>(tau[2], a.w, w2);
+                }
                 const long long dst = a.perm[i];
                 for (int bb = 0; bb < nb; ++bb) {
                     const CT v = contract<T, D, W>(box + bb * slot, a.g, lb, w0, w1, w2, a.comp != 0, nw);
@@ -771,6 +822,112 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
     }
 }
 
+// Fixed-point cells of the d = 2 / d = 3 spreading boxes (16 bytes per cell).
+//  FP32: each component holds v = hi * 2^21 + lo in two int32 words, with
+//    the quantum chosen so that the item's total stays below 2^42 quanta.  A
+//    value X (in quanta, |X| < 2^43) splits exactly with float arithmetic:
+//    hi = rint(X 2^-21) and lo = rint(X - hi 2^21), |lo| <= 2^20, both read
+//    off the bits of y + 1.5 * 2^23 (valid for |y| < 2^22).  An item adds at
+//    most 2047 times to a cell, so neither word can overflow, and integer
+//    addition keeps the sum exact and independent of order.  32-bit shared
+//    atomics are several times faster than 64-bit ones, and no step needs
+//    the FP64 pipe (slow on this part).
+//  FP64: one 64-bit word per component, total below 2^62 quanta.
+template <typename T> struct FixedCell;
+template <> struct FixedCell<float> {
+    static constexpr int kBits = 42;
+    static constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
+    static constexpr int kMagicBits = 0x4B400000;
+    __device__ static void add(unsigned char* cell, float xr, float xi) {
+        int* w = reinterpret_cast<int*>(cell);
+        split(w, xr);
+        split(w + 2, xi);
+    }
+    __device__ static void split(int* w, float X) {
+        const float h = fmaf(X, 0x1p-21f, kMagic);
+        const int hi = __float_as_int(h) - kMagicBits;
+        const float lo_f = fmaf(-(h - kMagic), 0x1p21f, X);
+        const int lo = __float_as_int(lo_f + kMagic) - kMagicBits;
+        if (hi != 0) atomicAdd(w, hi);
+        if (lo != 0) atomicAdd(w + 1, lo);
+    }
+    // (hi 2^21 + lo) q rounded once to float; q_hi = q 2^21 (powers of two).
+    __device__ static float value(const unsigned char* cell, int comp, float q, float q_hi) {
+        const int* w = reinterpret_cast<const int*>(cell) + 2 * comp;
+        const int c = w[1] >> 21;                  // carry: lo = c 2^21 + r, 0 <= r < 2^21
+        const int hi = w[0] + c;                   // |hi| < 2^22
+        const int r = w[1] - c * 2097152;
+        const float hf = __int_as_float(hi + kMagicBits) - kMagic;   // exact for |x| < 2^22
+        const float rf = __int_as_float(r + kMagicBits) - kMagic;
+        return fmaf(hf, q_hi, rf * q);
+    }
+};
+template <> struct FixedCell<double> {
+    static constexpr int kBits = 62;
+    __device__ static void add(unsigned char* cell, double xr, double xi) {
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(cell);
+        const long long vr = __double2ll_rn(xr), vi = __double2ll_rn(xi);
+        if (vr != 0) atomicAdd(w, static_cast<unsigned long long>(vr));
+        if (vi != 0) atomicAdd(w + 1, static_cast<unsigned long long>(vi));
+    }
+    __device__ static double value(const unsigned char* cell, int comp, double q, double) {
+        return static_cast<double>(reinterpret_cast<const long long*>(cell)[comp]) * q;
+    }
+};
+
+// Bound on an item's total |input| (both components, all batch entries of
+// the group) for the quantum of the fixed-point box, reduced over the block
+// into s_red[0 .. nwarps).  FP32 inputs are summed in FP32: the relative
+// error of the sum, below (count) 2^-24, is covered by the margin the
+// caller applies.
+template <typename T>
+__device__ __forceinline__ void item_abs_sum(const TapArgs<T>& a, const WorkItem& wi, int b0, int nb, double* s_red) {
+    using CT = C2<T>;
+    T part = T(0);
+    for (int j = threadIdx.x; j < wi.count; j += blockDim.x) {
+        const long long src = a.perm[wi.start + j];
+        for (int bb = 0; bb < nb; ++bb) {
+            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
+            part += FM<T>::abs(gv.x) + FM<T>::abs(gv.y);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = static_cast<double>(part);
+}
+
+// Thread 0: quantum q = 2^(e - bits) with 2^e above the item's bound (the
+// summed |input| times the window-product bound, with a 1e-3 margin).
+template <typename T>
+__device__ __forceinline__ void item_quantum(const TapArgs<T>& a, int nwarps, double* s_red) {
+    double tot = 0.0;
+    for (int w = 0; w < nwarps; ++w) tot += s_red[w];
+    tot *= static_cast<double>(a.wbound) * 1.001;
+    int e = 0;
+    if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e
+    s_red[32] = ldexp(1.0, e - FixedCell<T>::kBits);
+    s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
+    // the same powers of two in the plan precision: 1/q, q, q 2^21, flag
+    T* f = reinterpret_cast<T*>(s_red + 36);
+    f[0] = static_cast<T>(ldexp(1.0, FixedCell<T>::kBits - e));
+    f[1] = static_cast<T>(s_red[32]);
+    f[2] = static_cast<T>(ldexp(1.0, e - FixedCell<T>::kBits + 21));
+    f[3] = (tot > 0.0) ? T(1) : T(0);
+}
+
+// Reads back what item_quantum stored.
+template <typename T>
+struct ItemQuantum {
+    T inv_q, q_lo, q_hi;
+    bool any;
+    __device__ explicit ItemQuantum(const double* s_red) {
+        const T* f = reinterpret_cast<const T*>(s_red + 36);
+        inv_q = f[0];
+        q_lo = f[1];
+        q_hi = f[2];
+        any = f[3] != T(0);
+    }
+};
+
 // d = 2 spreading without block barriers inside a work item: warp w walks a
 // contiguous share of the item's (cell-sorted) nodes in chunks of 32.
 //  Phase A: lane l evaluates the 2 x 2m window values of chunk node l (one
@@ -803,6 +960,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
     U* boxu = reinterpret_cast<U*>(smem + Ls.box);
     T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
     double* s_red = reinterpret_cast<double*>(smem + Ls.red);
+    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
@@ -810,35 +968,18 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
         tile_origin<2>(a.g, wi.tile, periodic, org);
         for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
             const int nb = min(nbmax, a.batch - b0);
-            double part = 0.0;
-            for (int j = tid; j < wi.count; j += blockDim.x) {
-                const long long src = a.perm[wi.start + j];
-                for (int bb = 0; bb < nb; ++bb) {
-                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
-                }
-            }
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-            if (lane == 0) s_red[warp] = part;
+            item_abs_sum<T>(a, wi, b0, nb, s_red);
             for (int idx = tid; idx < nb * slot * 2; idx += blockDim.x) boxu[idx] = 0ull;
             __syncthreads();
-            if (tid == 0) {
-                double tot = 0.0;
-                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-                tot *= static_cast<double>(a.wbound) * 1.0001;
-                int e = 0;
-                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e; 2^(62-e) stays a finite float
-                s_red[32] = ldexp(1.0, e - 62);                // quantum q
-                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
-            }
+            if (tid == 0) item_quantum<T>(a, nwarps, s_red);
             __syncthreads();
-            const double qd = s_red[32];
-            const T inv_q = static_cast<T>(1.0 / qd);
-            if (s_red[33] != 0.0) {
+            const ItemQuantum<T> iq(s_red);
+            const T inv_q = iq.inv_q, q_lo = iq.q_lo, q_hi = iq.q_hi;
+            if (iq.any) {
                 const int per = (wi.count + nwarps - 1) / nwarps;
                 const int jlo = warp * per, jhi = min(wi.count, jlo + per);
                 for (int bb = 0; bb < nb; ++bb) {
-                    U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
+                    unsigned char* bx = reinterpret_cast<unsigned char*>(boxu + static_cast<size_t>(bb) * slot * 2);
                     int seg = -1, seg_lb0 = 0, col = 0;
                     T ar[A], ai[A];
 #pragma unroll
@@ -849,8 +990,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             for (int q = 0; q < A; ++q) {
                                 if (q < nw) {
                                     const int cell = (seg_lb0 + q) * box1 + col;
-                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
-                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
+                                    FixedCell<T>::add(bx + static_cast<size_t>(cell) * 16, ar[q], ai[q]);
                                 }
                             }
                         }
@@ -864,18 +1004,11 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             int lb[3] = {0, 0, 0};
                             node_setup<T, 2>(a.xs, i, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-                            T wt[A];
-                            tap_weights<T, W>(tau[0], a.w, wt);
-#pragma unroll
-                            for (int q = 0; q < A; ++q)
-                                if (q < nw) row[q] = wt[q];
-                            tap_weights<T, W>(tau[1], a.w, wt);
-#pragma unroll
-                            for (int q = 0; q < A; ++q)
-                                if (q < nw) row[A + q] = wt[q];
+                            tap_weights_to<T, W>(row, fast, tau[0], a.w);
+                            tap_weights_to<T, W>(row + A, fast, tau[1], a.w);
                             const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
-                            row[2 * A] = gv.x;
-                            row[2 * A + 1] = gv.y;
+                            row[2 * A] = gv.x * inv_q;
+                            row[2 * A + 1] = gv.y * inv_q;
                             reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
                         }
                         __syncwarp();
@@ -917,61 +1050,16 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
             for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
                 const int bb = idx / box_cells;
                 const int cell = idx - bb * box_cells;
-                const U* u = boxu + (static_cast<size_t>(bb) * slot + cell) * 2;
+                const unsigned char* c = reinterpret_cast<const unsigned char*>(boxu + (static_cast<size_t>(bb) * slot + cell) * 2);
                 CT v;
-                v.x = static_cast<T>(static_cast<double>(static_cast<long long>(u[0])) * qd);
-                v.y = static_cast<T>(static_cast<double>(static_cast<long long>(u[1])) * qd);
+                v.x = FixedCell<T>::value(c, 0, q_lo, q_hi);
+                v.y = FixedCell<T>::value(c, 1, q_lo, q_hi);
                 a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
             }
             __syncthreads();
         }
     }
 }
-
-// Fixed-point cells of the d = 3 spreading box (16 bytes per cell).
-//  FP32: each component holds v = hi * 2^21 + lo in two int32 words, with
-//    the quantum chosen so that the item's total stays below 2^42 quanta.  A
-//    value X (in quanta, |X| < 2^42) splits exactly with float arithmetic:
-//    hi = rint(X 2^-21) and lo = rint(X - hi 2^21), |lo| <= 2^20, both read
-//    off the bits of y + 1.5 * 2^23 (valid for |y| < 2^22).  An item adds at
-//    most 2047 times to a cell, so neither word can overflow, and integer
-//    addition keeps the sum exact and independent of order.  32-bit shared
-//    atomics are several times faster than 64-bit ones.
-//  FP64: one 64-bit word per component, total below 2^62 quanta.
-template <typename T> struct Fixed3;
-template <> struct Fixed3<float> {
-    static constexpr int kBits = 42;
-    __device__ static void add(unsigned char* cell, float xr, float xi) {
-        int* w = reinterpret_cast<int*>(cell);
-        split(w, xr);
-        split(w + 2, xi);
-    }
-    __device__ static void split(int* w, float X) {
-        const float magic = 12582912.0f;   // 1.5 * 2^23
-        const float h = fmaf(X, 0x1p-21f, magic);
-        const int hi = __float_as_int(h) - 0x4B400000;
-        const float lo_f = fmaf(-(h - magic), 0x1p21f, X);
-        const int lo = __float_as_int(lo_f + magic) - 0x4B400000;
-        if (hi != 0) atomicAdd(w, hi);
-        if (lo != 0) atomicAdd(w + 1, lo);
-    }
-    __device__ static double value(const unsigned char* cell, int comp) {
-        const int* w = reinterpret_cast<const int*>(cell) + 2 * comp;
-        return static_cast<double>(static_cast<long long>(w[0]) * (1ll << 21) + static_cast<long long>(w[1]));
-    }
-};
-template <> struct Fixed3<double> {
-    static constexpr int kBits = 62;
-    __device__ static void add(unsigned char* cell, double xr, double xi) {
-        unsigned long long* w = reinterpret_cast<unsigned long long*>(cell);
-        const long long vr = __double2ll_rn(xr), vi = __double2ll_rn(xi);
-        if (vr != 0) atomicAdd(w, static_cast<unsigned long long>(vr));
-        if (vi != 0) atomicAdd(w + 1, static_cast<unsigned long long>(vi));
-    }
-    __device__ static double value(const unsigned char* cell, int comp) {
-        return static_cast<double>(reinterpret_cast<const long long*>(cell)[comp]);
-    }
-};
 
 // d = 3 spreading.  Warp w walks a contiguous share of the item's (cell-
 // sorted) nodes in chunks of 32: lane l first evaluates the 3 x 2m window
@@ -1000,6 +1088,7 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
     unsigned long long* boxz = reinterpret_cast<unsigned long long*>(smem + Ls.box);
     T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
     double* s_red = reinterpret_cast<double*>(smem + Ls.red);
+    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
@@ -1007,31 +1096,14 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
         tile_origin<3>(a.g, wi.tile, periodic, org);
         for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
             const int nb = min(nbmax, a.batch - b0);
-            double part = 0.0;
-            for (int j = tid; j < wi.count; j += blockDim.x) {
-                const long long src = a.perm[wi.start + j];
-                for (int bb = 0; bb < nb; ++bb) {
-                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
-                }
-            }
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-            if (lane == 0) s_red[warp] = part;
+            item_abs_sum<T>(a, wi, b0, nb, s_red);
             for (int idx = tid; idx < nb * box_cells * 2; idx += blockDim.x) boxz[idx] = 0ull;
             __syncthreads();
-            if (tid == 0) {
-                double tot = 0.0;
-                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-                tot *= static_cast<double>(a.wbound) * 1.0001;
-                int e = 0;
-                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e
-                s_red[32] = ldexp(1.0, e - Fixed3<T>::kBits);   // quantum q
-                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
-            }
+            if (tid == 0) item_quantum<T>(a, nwarps, s_red);
             __syncthreads();
-            const double qd = s_red[32];
-            const T inv_q = static_cast<T>(1.0 / qd);
-            if (s_red[33] != 0.0) {
+            const ItemQuantum<T> iq(s_red);
+            const T inv_q = iq.inv_q, q_lo = iq.q_lo, q_hi = iq.q_hi;
+            if (iq.any) {
                 const int per = (wi.count + nwarps - 1) / nwarps;
                 const int jlo = warp * per, jhi = min(wi.count, jlo + per);
                 for (int bb = 0; bb < nb; ++bb) {
@@ -1045,14 +1117,8 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                             int lb[3] = {0, 0, 0};
                             node_setup<T, 3>(a.xs, i, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-                            T wt[A];
 #pragma unroll
-                            for (int t = 0; t < 3; ++t) {
-                                tap_weights<T, W>(tau[t], a.w, wt);
-#pragma unroll
-                                for (int q = 0; q < A; ++q)
-                                    if (q < nw) row[t * A + q] = wt[q];
-                            }
+                            for (int t = 0; t < 3; ++t) tap_weights_to<T, W>(row + t * A, fast, tau[t], a.w);
                             const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
                             row[3 * A] = gv.x * inv_q;
                             row[3 * A + 1] = gv.y * inv_q;
@@ -1093,7 +1159,7 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                                     const int pitch0 = bx1 * bx2;
 #pragma unroll
                                     for (int q = 0; q < A; ++q)
-                                        if (q < nw) Fixed3<T>::add(bx + static_cast<size_t>(base + q * pitch0) * 16, ar[q], ai[q]);
+                                        if (q < nw) FixedCell<T>::add(bx + static_cast<size_t>(base + q * pitch0) * 16, ar[q], ai[q]);
                                 }
                             }
                             k = k1;
@@ -1108,8 +1174,8 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                 const int cell = idx - bb * box_cells;
                 const unsigned char* c = boxc + (static_cast<size_t>(bb) * box_cells + cell) * 16;
                 CT v;
-                v.x = static_cast<T>(Fixed3<T>::value(c, 0) * qd);
-                v.y = static_cast<T>(Fixed3<T>::value(c, 1) * qd);
+                v.x = FixedCell<T>::value(c, 0, q_lo, q_hi);
+                v.y = FixedCell<T>::value(c, 1, q_lo, q_hi);
                 a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
             }
             __syncthreads();
