@@ -129,9 +129,11 @@ __device__ __forceinline__ T win_phi(T delta, const WinParams<T>& w) {
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
-    // sinh(beta s)/sinh(beta) = (e^{beta(s-1)} - e^{-beta(s+1)}) / (1 - e^{-2 beta})
+    // sinh(beta s)/sinh(beta) = (e^{beta(s-1)} - e^{-beta(s+1)}) / (1 - e^{-2 beta}),
+    // with s - 1 = -r^2 / (1 + s) (no cancellation)
     const T sq = FM<T>::sqrtw(q);
-    return (FM<T>::exp2w(w.c_exp * (sq - T(1))) - FM<T>::exp2w(-w.c_exp * (sq + T(1)))) * w.c_norm;
+    const T one_sq = T(1) + sq;
+    return (FM<T>::exp2w(-w.c_exp * FM<T>::div(r * r, one_sq)) - FM<T>::exp2w(-w.c_exp * one_sq)) * w.c_norm;
 }
 
 // d Phi / d delta; zero where |delta| >= m (the infinite edge derivative of
@@ -143,8 +145,10 @@ __device__ __forceinline__ T win_dphi(T delta, const WinParams<T>& w) {
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
     const T sq = FM<T>::sqrtw(q);
+    const T one_sq = T(1) + sq;
     const T ds = -r * w.inv_m / sq;
-    return w.beta * (FM<T>::exp2w(w.c_exp * (sq - T(1))) + FM<T>::exp2w(-w.c_exp * (sq + T(1)))) * w.c_norm * ds;
+    return w.beta * (FM<T>::exp2w(-w.c_exp * FM<T>::div(r * r, one_sq)) + FM<T>::exp2w(-w.c_exp * one_sq)) *
+           w.c_norm * ds;
 }
 
 // Tap count per dimension: W = 2m fixed at compile time, or W = 0 for a
@@ -155,6 +159,11 @@ template <int W> struct TapN {
 
 // One Shannon / sinh tap weight (the FAST case of tap_weights) for tap a;
 // s = sin(pi tau).
+//
+// The exponent beta (sqrt(q) - 1) / ln 2 (up to 18 at m = 8) would multiply
+// the relative error of sqrt(q) by that much; it is evaluated as
+// -c r^2 / (1 + sqrt(q)) instead, where that error is damped.  One
+// reciprocal serves both 1/(1 + sqrt(q)) and the sinc's 1/(pi delta).
 template <typename T>
 __device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
     const int n = m - 1 - a;
@@ -163,9 +172,15 @@ __device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const
     const T q = fma(-r, r, T(1));
     const bool in = q > T(0);
     const T sq = FM<T>::sqrtw(in ? q : T(1));
-    const T ph = (FM<T>::exp2w(wp.c_exp * (sq - T(1))) - FM<T>::exp2w(-wp.c_exp * (sq + T(1)))) * wp.c_norm;
+    const T one_sq = T(1) + sq;
+    const bool centre = delta == T(0);
+    const T den = centre ? T(1) : static_cast<T>(kPiD) * delta;
+    const T rc = FM<T>::div(T(1), den * one_sq);        // 1 / (pi delta (1 + sqrt q))
+    const T e1 = FM<T>::exp2w(-wp.c_exp * (r * r) * (rc * den));
+    const T e2 = FM<T>::exp2w(-wp.c_exp * one_sq);
+    const T ph = (e1 - e2) * wp.c_norm;
     const T num = (n & 1) ? -s : s;
-    const T sc = (delta == T(0)) ? T(1) : FM<T>::div(num, static_cast<T>(kPiD) * delta);
+    const T sc = centre ? T(1) : num * (rc * one_sq);
     return in ? sc * ph : T(0);
 }
 
