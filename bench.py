@@ -309,6 +309,7 @@ def run_ours(args, cfg):
         if rank == 0:
             print(json.dumps({"quick": True, "config": cfg, "ms_per_step": t_step, "value": world * N / (t_step * 1e-3),
                               "unit": UNIT, "gpu_launches": launches, "clocks": clk,
+                              "set_nodes_ms": float(np.median(set_ms)),
                               "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in ktimes.items()}}))
         if world > 1:
             dist.destroy_process_group()

@@ -22,7 +22,6 @@ namespace {
 constexpr int kRsThreads = 256;
 constexpr int kRsRounds = 16;
 constexpr int kRsSeg = kRsThreads * kRsRounds;   // items per block
-constexpr int kScanThreads = 1024;
 
 template <typename T>
 __global__ void key_kernel(const T* __restrict__ x, long long N, TileGeom g, uint32_t* __restrict__ keys,
@@ -59,41 +58,88 @@ __global__ void rs_hist_kernel(const uint32_t* __restrict__ keys, long long N, i
     hist[static_cast<long long>(threadIdx.x) * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of n uint32 in place by one block; *total receives the sum.
-__global__ void scan_exclusive_kernel(uint32_t* __restrict__ a, long long n, uint32_t* __restrict__ total) {
-    __shared__ uint32_t warp_tot[32];
-    const int tid = threadIdx.x;
-    const long long chunk = (n + kScanThreads - 1) / kScanThreads;
-    const long long lo = tid * chunk;
-    const long long hi = min(n, lo + chunk);
-    uint32_t s = 0;
-    for (long long i = lo; i < hi; ++i) s += a[i];
-    // block-wide exclusive scan of s
-    const int lane = tid & 31, wid = tid >> 5;
-    uint32_t incl = s;
+// Exclusive scan of n uint32 in place, *total receiving the sum, in three
+// launches: per-tile sums (tiles of kScanTile consecutive values), one block
+// scanning the tile sums, then each tile scanned from its offset.  All loads
+// are coalesced; every integer result is exact.
+constexpr int kScanThreads = 256;
+constexpr int kScanRounds = 16;
+constexpr int kScanTile = kScanThreads * kScanRounds;
+
+// Block-wide inclusive scan of one value per thread (kScanThreads or 1024
+// threads); returns the inclusive prefix, *block_total the block's sum.
+template <int NT>
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp, uint32_t& block_total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = v;
     for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
     }
-    if (lane == 31) warp_tot[wid] = incl;
+    if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        uint32_t w = warp_tot[lane];
+        const uint32_t w = (lane < NT / 32) ? s_warp[lane] : 0u;
         uint32_t wi = w;
         for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += v;
+            const uint32_t u = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += u;
         }
-        warp_tot[lane] = wi - w;   // exclusive prefix of warp totals
+        s_warp[lane] = wi - w;                 // exclusive prefix of the warp sums
+        if (lane == 31) s_warp[32] = wi;       // block total
     }
     __syncthreads();
-    uint32_t run = warp_tot[wid] + incl - s;
-    for (long long i = lo; i < hi; ++i) {
-        const uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    const uint32_t res = incl + s_warp[wid];
+    block_total = s_warp[32];
+    __syncthreads();                           // s_warp is reused by the caller's next round
+    return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sum_kernel(const uint32_t* __restrict__ a, long long n,
+                                                                     uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_warp[33];
+    const long long base = static_cast<long long>(blockIdx.x) * kScanTile;
+    uint32_t s = 0;
+#pragma unroll
+    for (int r = 0; r < kScanRounds; ++r) {
+        const long long i = base + r * kScanThreads + threadIdx.x;
+        if (i < n) s += a[i];
     }
-    if (tid == kScanThreads - 1) *total = run;
+    uint32_t tot;
+    block_incl_scan<kScanThreads>(s, s_warp, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One block of 1024 threads: exclusive scan of the tile sums in rounds of
+// 1024 consecutive values; *total receives the grand total.
+__global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t* __restrict__ sums, long long nt,
+                                                         uint32_t* __restrict__ total) {
+    __shared__ uint32_t s_warp[33];
+    uint32_t carry = 0;
+    for (long long b = 0; b < nt; b += 1024) {
+        const long long i = b + threadIdx.x;
+        const uint32_t v = (i < nt) ? sums[i] : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan<1024>(v, s_warp, tot);
+        if (i < nt) sums[i] = carry + incl - v;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_apply_kernel(uint32_t* __restrict__ a, long long n,
+                                                                       const uint32_t* __restrict__ sums) {
+    __shared__ uint32_t s_warp[33];
+    const long long base = static_cast<long long>(blockIdx.x) * kScanTile;
+    uint32_t run = sums[blockIdx.x];
+    for (int r = 0; r < kScanRounds; ++r) {
+        const long long i = base + r * kScanThreads + threadIdx.x;
+        const uint32_t v = (i < n) ? a[i] : 0u;
+        uint32_t tot;
+        const uint32_t incl = block_incl_scan<kScanThreads>(v, s_warp, tot);
+        if (i < n) a[i] = run + incl - v;
+        run += tot;
+    }
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -195,6 +241,17 @@ inline unsigned grid1d(long long n, int threads) {
     return static_cast<unsigned>((n + threads - 1) / threads);
 }
 
+// Launch the three-phase scan of a[0 .. n); sums holds ceil(n / kScanTile)
+// values (at least one).
+inline void scan_exclusive(uint32_t* a, long long n, uint32_t* total, uint32_t* sums, cudaStream_t s,
+                           long long& launches) {
+    const long long nt = std::max<long long>(1, (n + kScanTile - 1) / kScanTile);
+    scan_tile_sum_kernel<<<static_cast<unsigned>(nt), kScanThreads, 0, s>>>(a, n, sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(sums, nt, total);
+    scan_tile_apply_kernel<<<static_cast<unsigned>(nt), kScanThreads, 0, s>>>(a, n, sums);
+    launches += 3;
+}
+
 }  // namespace
 
 nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
@@ -212,6 +269,9 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     const long long nblocks = std::max<long long>(1, (N + kRsSeg - 1) / kRsSeg);
     if ((st = ensure_buf(p, p->hist, 256 * nblocks * 4)) != NFFTBL_OK) return st;
     if ((st = ensure_buf(p, p->tile_off, (p->n_tiles + 1) * 4)) != NFFTBL_OK) return st;
+    const long long scan_n = std::max<long long>(256 * nblocks, p->n_tiles);
+    if ((st = ensure_buf(p, p->scan_tmp, ((scan_n + kScanTile - 1) / kScanTile + 1) * 4)) != NFFTBL_OK) return st;
+    uint32_t* scan_sums = static_cast<uint32_t*>(p->scan_tmp.p);
     // counters: [0] scan total of the radix sort; tile_items: first work item per tile
     if ((st = ensure_buf(p, p->counters, 16)) != NFFTBL_OK) return st;
     if ((st = ensure_buf(p, p->tile_items, (p->n_tiles + 1) * 4)) != NFFTBL_OK) return st;
@@ -240,10 +300,10 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
         for (int shift = 0; shift < p->key_bits; shift += 8) {
             rs_hist_kernel<<<static_cast<unsigned>(nblocks), 256, 0, s>>>(kA, N, shift, static_cast<int>(nblocks),
                                                                           hist);
-            scan_exclusive_kernel<<<1, kScanThreads, 0, s>>>(hist, 256 * nblocks, total);
+            scan_exclusive(hist, 256 * nblocks, total, scan_sums, s, p->launches);
             rs_scatter_kernel<<<static_cast<unsigned>(nblocks), kRsThreads, 0, s>>>(
                 kA, vA, kB, vB, N, shift, static_cast<int>(nblocks), hist);
-            p->launches += 3;
+            p->launches += 2;
             std::swap(kA, kB);
             std::swap(vA, vB);
         }
@@ -267,10 +327,10 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
     uint32_t* chunk_start = static_cast<uint32_t*>(p->tile_items.p);
     uint32_t* work_total = chunk_start + p->n_tiles;
     chunk_count_kernel<<<grid1d(p->n_tiles, 256), 256, 0, s>>>(off, p->n_tiles, K, chunk_start);
-    scan_exclusive_kernel<<<1, kScanThreads, 0, s>>>(chunk_start, p->n_tiles, work_total);
+    scan_exclusive(chunk_start, p->n_tiles, work_total, scan_sums, s, p->launches);
     emit_work_kernel<<<grid1d(p->n_tiles, 256), 256, 0, s>>>(off, chunk_start, p->n_tiles, K,
                                                              static_cast<WorkItem*>(p->work.p));
-    p->launches += 4;
+    p->launches += 3;
     timing_end(p);
     if ((st = check_cuda(p, cudaGetLastError(), "binning launch")) != NFFTBL_OK) return st;
     uint32_t host_total = 0;

@@ -234,6 +234,7 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->keys_tmp);
     free_buf(p->perm_tmp);
     free_buf(p->hist);
+    free_buf(p->scan_tmp);
     free_buf(p->tile_off);
     free_buf(p->work);
     free_buf(p->tile_items);

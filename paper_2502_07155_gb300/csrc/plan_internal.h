@@ -201,6 +201,7 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf keys, perm;         // sorted keys / permutation (uint32)
     nfftbl::DeviceBuf keys_tmp, perm_tmp; // radix sort ping-pong
     nfftbl::DeviceBuf hist;               // radix sort block histograms
+    nfftbl::DeviceBuf scan_tmp;           // per-tile sums of the multi-block scan
     nfftbl::DeviceBuf tile_off;           // n_tiles + 1 (uint32)
     nfftbl::DeviceBuf work;               // WorkItem list
     nfftbl::DeviceBuf tile_items;         // n_tiles + 1: first work item per tile
