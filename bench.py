@@ -56,16 +56,66 @@ CONFIGS = {
 }
 DEFAULT_CONFIG = "d2_M256_m8_N2^20"
 
-# GB300 unit counts (152 SMs, 128 FP32 lanes and 16 SFU lanes per SM) at the
-# maximum SM clock; the FP32 peak is the ALU roofline of the short-sum kernels.
+# GB300 unit counts at the maximum SM clock (2070 MHz): 152 SMs; 128 FP32
+# FMA lanes per SM; the special-function unit issues 16 lanes per SM per clock
+# for rsqrt / rcp and 32 for ex2 (measured with ``bench.py --unit-rates``).
+# The roofline of a short-sum kernel is the largest of its FP32 time, its SFU
+# time and its HBM time; the JSON reports the binding one.
 SMS = 152
 FP32_LANES = 128
+SFU_SLOTS = 16           # SFU issue slots per SM per clock (rsqrt, rcp: 1 slot; ex2: 1/2)
 SM_MAX_MHZ = 2070.0
+# SFU slots per tap weight of the sinh window: rsqrt + rcp + 2 ex2 (1/2 each)
+SFU_SLOTS_PER_WEIGHT = 3.0
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of this workload: filled from the committed profile summary of the
 # same kernel version, None when not yet captured.
 NCU_TRAFFIC_BYTES = {}
+
+
+def short_sum_roofline(d, m, N, B, M, seconds):
+    """Roofline of one interpolation or spreading launch (N nodes, batch B):
+    algorithmic FP32 flops 5 (2m)^d per node and batch entry, SFU slots
+    3 * d * 2m per node (one sinh-window weight per tap and dimension), HBM
+    bytes (4d + 8) per node and batch entry plus one pass over the L^d grid.
+    Reports the unit whose time bound is largest."""
+    f = SM_MAX_MHZ * 1e6
+    flops = 5.0 * (2 * m) ** d * N * B
+    slots = SFU_SLOTS_PER_WEIGHT * d * 2 * m * N
+    hbm_bytes = (4 * d + 8) * N * B + 8 * (2 * M) ** d * B
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    t = {"fp32": flops / (SMS * FP32_LANES * 2 * f), "sfu": slots / (SMS * SFU_SLOTS * f),
+         "hbm": hbm_bytes / hbm_peak}
+    unit = max(t, key=t.get)
+    if unit == "fp32":
+        out = {"bound": "alu", "achieved": flops / seconds / 1e12, "peak": SMS * FP32_LANES * 2 * f / 1e12,
+               "unit": "TFLOP/s", "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
+    elif unit == "sfu":
+        out = {"bound": "alu", "achieved": slots / seconds / 1e12, "peak": SMS * SFU_SLOTS * f / 1e12,
+               "unit": "Tslot/s (SFU)",
+               "peak_note": "SFU: 152 SMs x 16 issue slots x 2070 MHz; rsqrt, rcp 1 slot, ex2 1/2 (measured rates)"}
+    else:
+        out = {"bound": "hbm", "achieved": hbm_bytes / seconds / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
+               "peak_note": "measured copy bandwidth"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out["bound_unit"] = unit
+    out["t_bound_us"] = {k: v * 1e6 for k, v in t.items()}
+    out["flops_per_launch"] = flops
+    out["sfu_slots_per_launch"] = slots
+    out["hbm_bytes_per_launch"] = hbm_bytes
+    return out
+
+
+def run_unit_rates():
+    """Build and run the unit-rate microbenchmark (FP32 FMA, ex2, rsqrt, rcp
+    lane operations per SM per clock); prints one JSON line per unit."""
+    src = os.path.join(ROOT, "paper_2502_07155_gb300", "unit_rates.cu")
+    exe = os.path.join(ROOT, "paper_2502_07155_gb300", "_build", "unit_rates")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    return subprocess.run([exe]).returncode
 
 
 def measured_peaks():
@@ -398,13 +448,9 @@ def run_ours(args, cfg):
     dom = max(("interp", "spread"), key=lambda k: ktimes[k][0])
     dom_ms, dom_n = ktimes[dom]
     per_launch_s = dom_ms / max(dom_n, 1) * 1e-3
-    flops = 5.0 * (2 * m) ** d * N * B            # algorithmic FP32 flops per launch
-    achieved = flops / per_launch_s / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    traffic = NCU_TRAFFIC_BYTES.get((cfg, dom))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "flops_per_launch": flops,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)"}
+    roofline = short_sum_roofline(d, m, N, B, M, per_launch_s)
+    roofline["kernel"] = dom
+    roofline["traffic"] = NCU_TRAFFIC_BYTES.get((cfg, dom))
 
     result = None
     if rank == 0:
@@ -542,11 +588,15 @@ def main():
     ap.add_argument("--learned-m", type=int, nargs="+", default=[2, 3, 4], dest="learned_m")
     ap.add_argument("--learned-steps", type=int, default=1500, dest="learned_steps")
     ap.add_argument("--learned-lr", type=float, default=3e-3, dest="learned_lr")
+    ap.add_argument("--unit-rates", action="store_true", dest="unit_rates",
+                    help="measure FP32 FMA and SFU lane rates per SM (roofline peaks)")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no FP64, classical, end-to-end or oracle legs); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.unit_rates:
+        return run_unit_rates()
     if args.impl == "reference":
         return run_reference(args, args.config)
     if args.learned:

@@ -215,6 +215,11 @@ __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w
     }
 }
 
+// Write the 2m tap weights of two dimensions to d0[0 .. 2m-1] and
+// d1[0 .. 2m-1] (shared memory), the two dimensions' chains interleaved.
+template <typename T, int W>
+__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, bool fast, T tau0, T tau1, const WinParams<T>& wp);
+
 // Write the 2m tap weights of one dimension to dst[0 .. 2m-1] (shared
 // memory), one at a time.
 template <typename T, int W>
@@ -231,6 +236,23 @@ __device__ __forceinline__ void tap_weights_to(T* dst, bool fast, T tau, const W
 #pragma unroll
         for (int q = 0; q < TapN<W>::A; ++q)
             if (q < nw) dst[q] = wt[q];
+    }
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, bool fast, T tau0, T tau1, const WinParams<T>& wp) {
+    if (!fast) {
+        tap_weights_to<T, W>(d0, false, tau0, wp);
+        tap_weights_to<T, W>(d1, false, tau1, wp);
+        return;
+    }
+    const int m = W ? W / 2 : wp.m;
+    const int nw = 2 * m;
+    const T s0 = FM<T>::sinpi(tau0), s1 = FM<T>::sinpi(tau1);
+#pragma unroll 2
+    for (int a = 0; a < nw; ++a) {
+        d0[a] = shannon_sinh_weight(tau0, s0, a, m, wp);
+        d1[a] = shannon_sinh_weight(tau1, s1, a, m, wp);
     }
 }
 
@@ -333,6 +355,21 @@ __device__ __forceinline__ bool tile_origin(const TileGeom& g, int tile, bool pe
         if (periodic && (org[t] < 0 || org[t] + g.box[t] > g.L[t])) wrap = true;
     }
     return wrap;
+}
+
+// Per-node setup from the node's coordinates xv: for each dimension, tau and
+// the local first-tap index.
+template <typename T, int D>
+__device__ __forceinline__ void node_setup_v(const T (&xv)[3], const TileGeom& g, const int (&org)[3], T (&tau)[3],
+                                             int (&lb)[3], int m) {
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        const T u = mul_rn(static_cast<T>(g.L[t]), xv[t]);
+        const T fl = FM<T>::flr(u);
+        tau[t] = u - fl;
+        const int cell = static_cast<int>(fl) + g.L[t] / 2;
+        lb[t] = cell - (m - 1) - org[t];
+    }
 }
 
 // Per-node setup: for each dimension, tau and the local first-tap index.
@@ -849,29 +886,33 @@ __global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a)
 //    the FP64 pipe (slow on this part).
 //  FP64: one 64-bit word per component, total below 2^62 quanta.
 template <typename T> struct FixedCell;
+// A batch entry's box is a group of component planes of `slot` cells each
+// (FP32: hi_re, lo_re, hi_im, lo_im as int32; FP64: re, im as 64-bit), so
+// that lanes adding to consecutive cells touch consecutive words.
 template <> struct FixedCell<float> {
     static constexpr int kBits = 42;
     static constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
     static constexpr int kMagicBits = 0x4B400000;
-    __device__ static void add(unsigned char* cell, float xr, float xi) {
-        int* w = reinterpret_cast<int*>(cell);
-        split(w, xr);
-        split(w + 2, xi);
+    __device__ static void add(unsigned char* grp, int cell, int slot, float xr, float xi) {
+        int* w = reinterpret_cast<int*>(grp) + cell;
+        split(w, w + slot, xr);
+        split(w + 2 * slot, w + 3 * slot, xi);
     }
-    __device__ static void split(int* w, float X) {
+    __device__ static void split(int* hi_p, int* lo_p, float X) {
         const float h = fmaf(X, 0x1p-21f, kMagic);
         const int hi = __float_as_int(h) - kMagicBits;
         const float lo_f = fmaf(-(h - kMagic), 0x1p21f, X);
         const int lo = __float_as_int(lo_f + kMagic) - kMagicBits;
-        if (hi != 0) atomicAdd(w, hi);
-        if (lo != 0) atomicAdd(w + 1, lo);
+        if (hi != 0) atomicAdd(hi_p, hi);
+        if (lo != 0) atomicAdd(lo_p, lo);
     }
     // (hi 2^21 + lo) q rounded once to float; q_hi = q 2^21 (powers of two).
-    __device__ static float value(const unsigned char* cell, int comp, float q, float q_hi) {
-        const int* w = reinterpret_cast<const int*>(cell) + 2 * comp;
-        const int c = w[1] >> 21;                  // carry: lo = c 2^21 + r, 0 <= r < 2^21
+    __device__ static float value(const unsigned char* grp, int cell, int slot, int comp, float q, float q_hi) {
+        const int* w = reinterpret_cast<const int*>(grp) + 2 * comp * slot + cell;
+        const int lo = w[slot];
+        const int c = lo >> 21;                    // carry: lo = c 2^21 + r, 0 <= r < 2^21
         const int hi = w[0] + c;                   // |hi| < 2^22
-        const int r = w[1] - c * 2097152;
+        const int r = lo - c * 2097152;
         const float hf = __int_as_float(hi + kMagicBits) - kMagic;   // exact for |x| < 2^22
         const float rf = __int_as_float(r + kMagicBits) - kMagic;
         return fmaf(hf, q_hi, rf * q);
@@ -879,14 +920,14 @@ template <> struct FixedCell<float> {
 };
 template <> struct FixedCell<double> {
     static constexpr int kBits = 62;
-    __device__ static void add(unsigned char* cell, double xr, double xi) {
-        unsigned long long* w = reinterpret_cast<unsigned long long*>(cell);
+    __device__ static void add(unsigned char* grp, int cell, int slot, double xr, double xi) {
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(grp) + cell;
         const long long vr = __double2ll_rn(xr), vi = __double2ll_rn(xi);
         if (vr != 0) atomicAdd(w, static_cast<unsigned long long>(vr));
-        if (vi != 0) atomicAdd(w + 1, static_cast<unsigned long long>(vi));
+        if (vi != 0) atomicAdd(w + slot, static_cast<unsigned long long>(vi));
     }
-    __device__ static double value(const unsigned char* cell, int comp, double q, double) {
-        return static_cast<double>(reinterpret_cast<const long long*>(cell)[comp]) * q;
+    __device__ static double value(const unsigned char* grp, int cell, int slot, int comp, double q, double) {
+        return static_cast<double>(reinterpret_cast<const long long*>(grp)[comp * slot + cell]) * q;
     }
 };
 
@@ -899,11 +940,22 @@ template <typename T>
 __device__ __forceinline__ void item_abs_sum(const TapArgs<T>& a, const WorkItem& wi, int b0, int nb, double* s_red) {
     using CT = C2<T>;
     T part = T(0);
-    for (int j = threadIdx.x; j < wi.count; j += blockDim.x) {
-        const long long src = a.perm[wi.start + j];
+    const int step = blockDim.x;
+    for (int j0 = threadIdx.x; j0 < wi.count; j0 += 4 * step) {
+        uint32_t src[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * step;
+            src[u] = (j < wi.count) ? a.perm[wi.start + j] : 0xFFFFFFFFu;
+        }
         for (int bb = 0; bb < nb; ++bb) {
-            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-            part += FM<T>::abs(gv.x) + FM<T>::abs(gv.y);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (src[u] != 0xFFFFFFFFu) {
+                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src[u]];
+                    part += FM<T>::abs(gv.x) + FM<T>::abs(gv.y);
+                }
+            }
         }
     }
     for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
@@ -1004,36 +1056,54 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
 #pragma unroll
                             for (int q = 0; q < A; ++q) {
                                 if (q < nw) {
-                                    const int cell = (seg_lb0 + q) * box1 + col;
-                                    FixedCell<T>::add(bx + static_cast<size_t>(cell) * 16, ar[q], ai[q]);
+                                    FixedCell<T>::add(bx, (seg_lb0 + q) * box1 + col, slot, ar[q], ai[q]);
                                 }
                             }
                         }
                     };
+                    // node data of the next chunk, loaded one chunk ahead: coordinates
+                    // and permutation during phase A, the input value before phase B
+                    T nx[3] = {T(0), T(0), T(0)};
+                    uint32_t nperm = 0;
+                    CT ng = cmake<T>(T(0), T(0));
+                    auto load_xp = [&](int c) {
+                        if (c + lane < jhi) {
+                            const long long i = static_cast<long long>(wi.start) + c + lane;
+                            nx[0] = a.xs[i * 2];
+                            nx[1] = a.xs[i * 2 + 1];
+                            nperm = a.perm[i];
+                        }
+                    };
+                    auto load_g = [&](int c) {
+                        if (c + lane < jhi) ng = a.fin[static_cast<long long>(b0 + bb) * a.N + nperm];
+                    };
+                    load_xp(jlo);
+                    load_g(jlo);
                     for (int c0 = jlo; c0 < jhi; c0 += 32) {
                         const int nc = min(32, jhi - c0);
+                        const T cx[3] = {nx[0], nx[1], T(0)};
+                        const CT cg = ng;
+                        load_xp(c0 + 32);
                         // ---- phase A: this lane's node
                         if (lane < nc) {
-                            const long long i = static_cast<long long>(wi.start) + c0 + lane;
                             T tau[3];
                             int lb[3] = {0, 0, 0};
-                            node_setup<T, 2>(a.xs, i, a.g, org, tau, lb, m);
+                            node_setup_v<T, 2>(cx, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-                            tap_weights_to<T, W>(row, fast, tau[0], a.w);
-                            tap_weights_to<T, W>(row + A, fast, tau[1], a.w);
-                            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
-                            row[2 * A] = gv.x * inv_q;
-                            row[2 * A + 1] = gv.y * inv_q;
+                            tap_weights_to2<T, W>(row, row + A, fast, tau[0], tau[1], a.w);
+                            row[2 * A] = cg.x * inv_q;
+                            row[2 * A + 1] = cg.y * inv_q;
                             reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
                         }
                         __syncwarp();
-                        // ---- phase B: walk the chunk
-#pragma unroll 1
-                        for (int k = 0; k < nc; ++k) {
-                            const T* row = s_tab + k * RS;
+                        load_g(c0 + 32);
+                        // ---- phase B: walk the chunk (two nodes at a time while both
+                        // stay in the current segment)
+                        auto seg_key = [&](int lbk) { return (lbk & 0xFFFF) | (((lbk >> 16) / S) << 16); };
+                        auto one = [&](const T* row) {
                             const int lbk = reinterpret_cast<const int*>(row + 2 * A + 2)[0];
                             const int lb0 = lbk & 0xFFFF, lb1 = lbk >> 16;
-                            const int key = lb0 | ((lb1 / S) << 16);
+                            const int key = seg_key(lbk);
                             if (key != seg) {
                                 if (seg >= 0) flush();
                                 seg = key;
@@ -1055,7 +1125,40 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                                     ai[q] += gi * w0r[q];
                                 }
                             }
+                        };
+                        int k = 0;
+#pragma unroll 1
+                        for (; W != 0 && k + 1 < nc; k += 2) {   // (runtime-m kernels walk singly)
+                            const T* ra = s_tab + k * RS;
+                            const T* rb = ra + RS;
+                            const int la = reinterpret_cast<const int*>(ra + 2 * A + 2)[0];
+                            const int lbb = reinterpret_cast<const int*>(rb + 2 * A + 2)[0];
+                            if (seg_key(la) == seg && seg_key(lbb) == seg) {
+                                const int ta = col - (la >> 16), tb = col - (lbb >> 16);
+                                const bool ina = (ta >= 0) && (ta < nw), inb = (tb >= 0) && (tb < nw);
+                                const T wfa = ina ? ra[A + (ina ? ta : 0)] : T(0);
+                                const T wfb = inb ? rb[A + (inb ? tb : 0)] : T(0);
+                                const T gra = ra[2 * A] * wfa, gia = ra[2 * A + 1] * wfa;
+                                const T grb = rb[2 * A] * wfb, gib = rb[2 * A + 1] * wfb;
+                                T wa[A], wb[A];
+                                load_row<T, A>(ra, wa);
+                                load_row<T, A>(rb, wb);
+#pragma unroll
+                                for (int q = 0; q < A; ++q) {
+                                    if (q < nw) {
+                                        ar[q] += gra * wa[q];
+                                        ai[q] += gia * wa[q];
+                                        ar[q] += grb * wb[q];
+                                        ai[q] += gib * wb[q];
+                                    }
+                                }
+                            } else {
+                                one(ra);
+                                one(rb);
+                            }
                         }
+#pragma unroll 1
+                        for (; k < nc; ++k) one(s_tab + k * RS);
                         __syncwarp();
                     }
                     if (seg >= 0) flush();
@@ -1065,10 +1168,10 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
             for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
                 const int bb = idx / box_cells;
                 const int cell = idx - bb * box_cells;
-                const unsigned char* c = reinterpret_cast<const unsigned char*>(boxu + (static_cast<size_t>(bb) * slot + cell) * 2);
+                const unsigned char* grp = reinterpret_cast<const unsigned char*>(boxu + static_cast<size_t>(bb) * slot * 2);
                 CT v;
-                v.x = FixedCell<T>::value(c, 0, q_lo, q_hi);
-                v.y = FixedCell<T>::value(c, 1, q_lo, q_hi);
+                v.x = FixedCell<T>::value(grp, cell, slot, 0, q_lo, q_hi);
+                v.y = FixedCell<T>::value(grp, cell, slot, 1, q_lo, q_hi);
                 a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
             }
             __syncthreads();
@@ -1174,7 +1277,7 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                                     const int pitch0 = bx1 * bx2;
 #pragma unroll
                                     for (int q = 0; q < A; ++q)
-                                        if (q < nw) FixedCell<T>::add(bx + static_cast<size_t>(base + q * pitch0) * 16, ar[q], ai[q]);
+                                        if (q < nw) FixedCell<T>::add(bx, base + q * pitch0, box_cells, ar[q], ai[q]);
                                 }
                             }
                             k = k1;
@@ -1187,10 +1290,10 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
             for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
                 const int bb = idx / box_cells;
                 const int cell = idx - bb * box_cells;
-                const unsigned char* c = boxc + (static_cast<size_t>(bb) * box_cells + cell) * 16;
+                const unsigned char* grp = boxc + static_cast<size_t>(bb) * box_cells * 16;
                 CT v;
-                v.x = FixedCell<T>::value(c, 0, q_lo, q_hi);
-                v.y = FixedCell<T>::value(c, 1, q_lo, q_hi);
+                v.x = FixedCell<T>::value(grp, cell, box_cells, 0, q_lo, q_hi);
+                v.y = FixedCell<T>::value(grp, cell, box_cells, 1, q_lo, q_hi);
                 a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
             }
             __syncthreads();
