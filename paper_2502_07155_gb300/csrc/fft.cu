@@ -44,7 +44,21 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
     CT* bufB = bufA + W * pitch;
     CT* twd = bufB + W * pitch;
     const int tid = threadIdx.x;
-    for (int j = tid; j < L; j += blockDim.x) twd[j] = tw[j];
+    const int bd = blockDim.x;
+    constexpr int kBatch = 8;   // global loads issued together before their shared-memory stores
+    for (int j0 = 0; j0 < L; j0 += kBatch * bd) {
+        CT v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int j = j0 + u * bd + tid;
+            if (j < L) v[u] = tw[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int j = j0 + u * bd + tid;
+            if (j < L) twd[j] = v[u];
+        }
+    }
 
     const int n_in = ADJ ? L : M;
     const int n_out = ADJ ? M : L;
@@ -67,28 +81,52 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
             bufA[w * pitch + zlo + idx % (zhi - zlo)] = cmake<T>(T(0), T(0));
         }
     }
-    for (int idx = tid; idx < W * n_in; idx += blockDim.x) {
-        int w, p;
-        long long g;
-        if (inner == 1) {
-            w = idx / n_in;
-            p = idx - w * n_in;
-            g = (o0 + w) * n_in + p;
-        } else {
-            p = idx / W;
-            w = idx - p * W;
-            g = (o0 * n_in + p) * static_cast<long long>(inner) + i0 + w;
+    for (int idx0 = 0; idx0 < W * n_in; idx0 += kBatch * bd) {
+        CT v[kBatch];
+        T f[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = idx0 + u * bd + tid;
+            v[u] = cmake<T>(T(0), T(0));
+            f[u] = T(1);
+            if (idx < W * n_in) {
+                int w, p;
+                long long g;
+                if (inner == 1) {
+                    w = idx / n_in;
+                    p = idx - w * n_in;
+                    g = (o0 + w) * n_in + p;
+                } else {
+                    p = idx / W;
+                    w = idx - p * W;
+                    g = (o0 * n_in + p) * static_cast<long long>(inner) + i0 + w;
+                }
+                if (w < nl) v[u] = in[g];
+                if (!ADJ) f[u] = fac[p];
+            }
         }
-        CT v = cmake<T>(T(0), T(0));
-        if (w < nl) v = in[g];
-        int q = p;
-        if (!ADJ) {
-            const T f = fac[p];
-            v.x *= f;
-            v.y *= f;
-            q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = idx0 + u * bd + tid;
+            if (idx < W * n_in) {
+                int w, p;
+                if (inner == 1) {
+                    w = idx / n_in;
+                    p = idx - w * n_in;
+                } else {
+                    p = idx / W;
+                    w = idx - p * W;
+                }
+                int q = p;
+                CT val = v[u];
+                if (!ADJ) {
+                    val.x *= f[u];
+                    val.y *= f[u];
+                    q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+                }
+                bufA[w * pitch + q] = val;
+            }
         }
-        bufA[w * pitch + q] = v;
     }
     __syncthreads();
 
@@ -181,12 +219,21 @@ size_t fft_smem(int L, int W) {
     return (2 * static_cast<size_t>(W) * (L + 1) + L) * sizeof(C2<T>);
 }
 
+// Lines per CTA: as many as fit in 64 KB of shared memory (up to 16, for
+// wide coalesced segments on the strided passes) while the launch still has
+// about four CTAs per SM; the lines of one CTA share one outer index.
 template <typename T>
-int choose_lines(int L, long long inner) {
+int choose_lines(int L, long long lines, long long inner, int num_sms) {
     int W = 16;
-    while (W > 1 && fft_smem<T>(L, W) > 64 * 1024) W >>= 1;
+    while (W > 1 && (fft_smem<T>(L, W) > 64 * 1024 || lines / W < 4LL * num_sms)) W >>= 1;
     if (inner > 1) W = static_cast<int>(std::min<long long>(W, inner));
     return W;
+}
+
+// Threads per CTA: one radix-4 butterfly per thread per stage, 64 .. 256.
+inline int fft_threads(int L, int W) {
+    const int t = (W * L / 4 + 31) / 32 * 32;
+    return std::max(64, std::min(kFftThreads, t));
 }
 
 template <typename T, bool ADJ>
@@ -196,7 +243,8 @@ nfftbl_status run_pass(nfftbl_plan_s* p, const void* in, void* out, int t) {
     long long inner = 1;
     for (int s = t + 1; s < p->d; ++s) inner *= p->L[s];
     const int L = p->L[t], M = p->M[t];
-    const int W = choose_lines<T>(L, inner);
+    const int W = choose_lines<T>(L, outer * inner, inner, p->num_sms);
+    const int threads = fft_threads(L, W);
     const size_t smem = fft_smem<T>(L, W);
     auto kern = fft_pass_kernel<T, ADJ>;
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -205,7 +253,7 @@ nfftbl_status run_pass(nfftbl_plan_s* p, const void* in, void* out, int t) {
     if (st != NFFTBL_OK) return st;
     long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
     timing_begin(p, NFFTBL_K_FFT);
-    kern<<<static_cast<unsigned>(blocks), kFftThreads, smem, p->stream>>>(
+    kern<<<static_cast<unsigned>(blocks), threads, smem, p->stream>>>(
         static_cast<const C2<T>*>(in), static_cast<C2<T>*>(out), outer, static_cast<int>(inner), M, L, W,
         static_cast<const T*>(p->facT[t].p), static_cast<const C2<T>*>(p->tw[t].p));
     timing_end(p);
@@ -247,13 +295,18 @@ nfftbl_status adjoint_impl(nfftbl_plan_s* p, void* fhat) {
 // extent (outer / inner line counts), for callers that own every buffer.
 cudaError_t launch_fft_forward_pass_f32(const void* in, void* out, long long outer, long long inner, int M, int L,
                                         const float* fac, const void* tw, cudaStream_t s) {
-    const int W = choose_lines<float>(L, inner);
+    int dev = 0, num_sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int W = choose_lines<float>(L, outer * inner, inner, num_sms);
+    const int threads = fft_threads(L, W);
     const size_t smem = fft_smem<float>(L, W);
     auto kern = fft_pass_kernel<float, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
-    kern<<<static_cast<unsigned>(blocks), kFftThreads, smem, s>>>(
+    kern<<<static_cast<unsigned>(blocks), threads, smem, s>>>(
         static_cast<const float2*>(in), static_cast<float2*>(out), outer, static_cast<int>(inner), M, L, W, fac,
         static_cast<const float2*>(tw));
     return cudaGetLastError();

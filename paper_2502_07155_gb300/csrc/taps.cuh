@@ -484,6 +484,92 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
     }
 }
 
+// Contraction of one batch entry for the Shannon / sinh plan (d >= 2) with
+// the dimension-0 weights evaluated inside the row loop: each is used once,
+// so they need no registers across the loop, and their SFU work overlaps
+// the rows' shared-memory loads and FMAs.  w1 (and w2) hold the other
+// dimensions' weights; s0 = sin(pi tau0).
+template <typename T, int D, int W>
+__device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, const TileGeom& g, const int (&lb)[3],
+                                                T tau0, T s0, const T (&w1)[TapN<W>::A], const T (&w2)[TapN<W>::A],
+                                                const WinParams<T>& wp, int nw_rt) {
+    const int nw = W ? W : nw_rt;
+    const int m = nw / 2;
+    T ar = T(0), ai = T(0);
+    if (D == 2) {
+        const int pitch = g.box[1];
+        const C2<T>* p = box + lb[0] * pitch + lb[1];
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) {
+            const T w0a = shannon_sinh_weight(tau0, s0, a, m, wp);
+            const C2<T>* row = p + a * pitch;
+            T rr = T(0), ri = T(0);
+#pragma unroll
+            for (int b = 0; b < TapN<W>::A; ++b) {
+                if (b < nw) {
+                    const C2<T> v = row[b];
+                    rr += v.x * w1[b];
+                    ri += v.y * w1[b];
+                }
+            }
+            ar += rr * w0a;
+            ai += ri * w0a;
+        }
+    } else {
+        const int p1 = g.box[2];
+        const int p0 = g.box[1] * p1;
+        const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
+        for (int a = 0; a < nw; ++a) {
+            const T w0a = shannon_sinh_weight(tau0, s0, a, m, wp);
+            T mr = T(0), mi = T(0);
+#pragma unroll 2
+            for (int b = 0; b < nw; ++b) {
+                const C2<T>* row = p + a * p0 + b * p1;
+                T rr = T(0), ri = T(0);
+#pragma unroll
+                for (int c = 0; c < TapN<W>::A; ++c) {
+                    if (c < nw) {
+                        const C2<T> v = row[c];
+                        rr += v.x * w2[c];
+                        ri += v.y * w2[c];
+                    }
+                }
+                mr += rr * w1[b];
+                mi += ri * w1[b];
+            }
+            ar += mr * w0a;
+            ai += mi * w0a;
+        }
+    }
+    return cmake<T>(ar, ai);
+}
+
+// One node of interp_kernel for every plan other than the single-batch
+// Shannon / sinh case (other windows, the classical method, batches,
+// compensated sums): all weights in registers, then one contraction per
+// batch entry.  Kept out of line so that its registers do not count
+// against the common path.
+template <typename T, int D, int W>
+__device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&lb)[3],
+                                                 const T (&tau)[3], bool fast, int b0, int nb, long long dst) {
+    constexpr int A = TapN<W>::A;
+    const int nw = W ? W : 2 * a.w.m;
+    T w0[A], w1[A], w2[A];
+    if (fast) {
+        tap_weights<T, W, true>(tau[0], a.w, w0);
+        if (D > 1) tap_weights<T, W, true>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
+    } else {
+        tap_weights<T, W>(tau[0], a.w, w0);
+        if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W>(tau[2], a.w, w2);
+    }
+    for (int bb = 0; bb < nb; ++bb) {
+        const C2<T> v = contract<T, D, W>(box + bb * slot, a.g, lb, w0, w1, w2, a.comp != 0, nw);
+        a.fout[static_cast<long long>(b0 + bb) * a.N + dst] = v;
+    }
+}
+
 // Stage the box(es) of batch entries b0 .. b0+nb-1 in shared memory.
 // Returns false if the copy did not complete within the wait limit.
 // Box slots in shared memory: each batch entry's box starts on a 128-byte
@@ -588,21 +674,16 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 T tau[3];
                 int lb[3] = {0, 0, 0};
                 node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
-                T w0[A], w1[A], w2[A];
-                if (fast) {
-                    tap_weights<T, W, true>(tau[0], a.w, w0);
-                    if (D > 1) tap_weights<T, W, true>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
-                } else {
-                    tap_weights<T, W>(tau[0], a.w, w0);
-                    if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W>(tau[2], a.w, w2);
-                }
                 const long long dst = a.perm[i];
-                for (int bb = 0; bb < nb; ++bb) {
-                    const CT v = contract<T, D, W>(box + bb * slot, a.g, lb, w0, w1, w2, a.comp != 0, nw);
-                    a.fout[static_cast<long long>(b0 + bb) * a.N + dst] = v;
+                if (fast && D >= 2 && nb == 1 && a.comp == 0) {
+                    T w1[A], w2[A];
+                    tap_weights<T, W, true>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] =
+                        contract_lazy0<T, D, W>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    continue;
                 }
+                interp_node_general<T, D, W>(a, box, slot, lb, tau, fast, b0, nb, dst);
             }
             __syncthreads();
         }
