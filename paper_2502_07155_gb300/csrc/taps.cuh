@@ -36,11 +36,25 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 template <typename T> struct FM;
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <> struct FM<float> {
-    // window arithmetic of the FP32 path: hardware 2^x and reciprocal square
-    // root (a few ulp; the kernels' FP32 accumulation dominates the error)
+    // window arithmetic of the FP32 path: hardware 2^x, reciprocal and
+    // reciprocal square root, one SFU operation each (a few ulp; flush-to-
+    // zero: callers keep the arguments normal)
     __device__ static float exp2w(float x) { return ex2_approx(x); }
-    __device__ static float sqrtw(float x) { return x * rsqrtf(x); }
+    __device__ static float sqrtw(float x) { return x * rsqrt_approx(x); }
+    __device__ static float rcpw(float x) { return rcp_approx(x); }
     __device__ static float sinpi(float x) { return sinpif(x); }
     __device__ static float cospi(float x) { return cospif(x); }
     __device__ static float sqrt(float x) { return sqrtf(x); }
@@ -54,6 +68,7 @@ template <> struct FM<float> {
 template <> struct FM<double> {
     __device__ static double exp2w(double x) { return ::exp2(x); }
     __device__ static double sqrtw(double x) { return ::sqrt(x); }
+    __device__ static double rcpw(double x) { return 1.0 / x; }
     __device__ static double sinpi(double x) { return ::sinpi(x); }
     __device__ static double cospi(double x) { return ::cospi(x); }
     __device__ static double sqrt(double x) { return ::sqrt(x); }
@@ -170,12 +185,12 @@ __device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const
     const T delta = tau + static_cast<T>(n);
     const T r = delta * wp.inv_m;
     const T q = fma(-r, r, T(1));
-    const bool in = q > T(0);
+    const bool in = q > T(1e-30);   // below: the weight is < 1e-13 (and keeps FP32 operands normal)
     const T sq = FM<T>::sqrtw(in ? q : T(1));
     const T one_sq = T(1) + sq;
     const bool centre = delta == T(0);
     const T den = centre ? T(1) : static_cast<T>(kPiD) * delta;
-    const T rc = FM<T>::div(T(1), den * one_sq);        // 1 / (pi delta (1 + sqrt q))
+    const T rc = FM<T>::rcpw(den * one_sq);             // 1 / (pi delta (1 + sqrt q))
     const T e1 = FM<T>::exp2w(-wp.c_exp * (r * r) * (rc * den));
     const T e2 = FM<T>::exp2w(-wp.c_exp * one_sq);
     const T ph = (e1 - e2) * wp.c_norm;
