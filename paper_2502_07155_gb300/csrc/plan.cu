@@ -124,6 +124,7 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
         a.w.c_norm = T(1);
     a.w.table = static_cast<const T*>(p->window == NFFTBL_WIN_TABLE ? p->table_dev.p : nullptr);
     a.w.table_n = static_cast<int>(p->table_host.size()) - 1;
+    a.w.tcoef = (sizeof(T) == 4 && p->window == NFFTBL_WIN_TABLE) ? static_cast<const float4*>(p->table_coef.p) : nullptr;
     a.batch = p->batch;
     const size_t bb = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
     a.batch_smem = static_cast<int>(std::max<size_t>(1, std::min<size_t>(p->batch, kBoxBudget / bb)));
@@ -234,6 +235,7 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->keys_tmp);
     free_buf(p->perm_tmp);
     free_buf(p->hist);
+    free_buf(p->table_coef);
     free_buf(p->scan_tmp);
     free_buf(p->tile_off);
     free_buf(p->work);
@@ -472,8 +474,9 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
             tab64 = static_cast<const double*>(p->table_dev.p);
         } else {
             if ((st = ensure_buf(p, p->table_dev, n * sizeof(float))) != NFFTBL_OK) return plan_fail(p, st, "");
+            if ((st = ensure_buf(p, p->table_coef, n * sizeof(float4))) != NFFTBL_OK) return plan_fail(p, st, "");
             if ((st = check_cuda(p, launch_table_cast(tab64, static_cast<int>(n), static_cast<float*>(p->table_dev.p),
-                                                      s0),
+                                                      static_cast<float4*>(p->table_coef.p), s0),
                                  "table cast")) != NFFTBL_OK)
                 return plan_fail(p, st, "");
         }
@@ -682,7 +685,8 @@ nfftbl_status nfftbl_set_window_table(nfftbl_plan_t p, const double* table_dev, 
     if (st != NFFTBL_OK) return st;
     if (!dbl &&
         (st = check_cuda(p, launch_table_cast(static_cast<const double*>(t64), table_len,
-                                              static_cast<float*>(p->table_dev.p), p->stream),
+                                              static_cast<float*>(p->table_dev.p),
+                                              static_cast<float4*>(p->table_coef.p), p->stream),
                          "table cast")) != NFFTBL_OK)
         return st;
     for (int t = 0; t < p->d; ++t) {

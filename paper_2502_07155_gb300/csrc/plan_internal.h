@@ -25,6 +25,7 @@ struct WinParams {
     T c_norm;          // 1 / (1 - e^{-2 beta}) (sinh) or 1/(I0(beta) - 1) (cKB)
     const T* table;    // window table on u in [0, 1] (table window), device
     int table_n;       // number of intervals (table has table_n + 1 values)
+    const float4* tcoef;   // FP32 plans: per interval the Catmull-Rom cubic c0 + c1 t + c2 t^2 + c3 t^3
 };
 
 // Geometry of the node tiles and of the shared-memory boxes around them.
@@ -201,6 +202,7 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf keys, perm;         // sorted keys / permutation (uint32)
     nfftbl::DeviceBuf keys_tmp, perm_tmp; // radix sort ping-pong
     nfftbl::DeviceBuf hist;               // radix sort block histograms
+    nfftbl::DeviceBuf table_coef;         // FP32 table window: float4 cubic coefficients per interval
     nfftbl::DeviceBuf scan_tmp;           // per-tile sums of the multi-block scan
     nfftbl::DeviceBuf tile_off;           // n_tiles + 1 (uint32)
     nfftbl::DeviceBuf work;               // WorkItem list
@@ -246,7 +248,7 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
                                   cudaStream_t s);
 cudaError_t launch_cast_factors(const double* fac64, int M, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s);
-cudaError_t launch_table_cast(const double* in, int n, float* out, cudaStream_t s);
+cudaError_t launch_table_cast(const double* in, int n, float* out, float4* coef, cudaStream_t s);
 cudaError_t launch_window_table_grad(int L, int M, int m, int table_n, const double* dEdpsi, double* grad,
                                      cudaStream_t s);
 

@@ -199,19 +199,71 @@ __device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const
     return in ? sc * ph : T(0);
 }
 
+// Weight kinds of the inline paths (chosen once per kernel from the plan).
+enum : int {
+    WK_GENERIC = 0,     // any window / method: per-tap dispatch (out of line for cKB, table)
+    WK_SINH = 1,        // Shannon method, sinh window
+    WK_TABLE = 2,       // Shannon method, tabulated window (the learned phi_theta)
+};
+
+template <typename T>
+__device__ __forceinline__ int weight_kind(const WinParams<T>& w) {
+    if (w.method != NFFTBL_SHANNON) return WK_GENERIC;
+    if (w.window == NFFTBL_WIN_SINH) return WK_SINH;
+    if (w.window == NFFTBL_WIN_TABLE) return WK_TABLE;
+    return WK_GENERIC;
+}
+
+// One Shannon / tabulated-window tap weight: sinc(pi delta) times the
+// Catmull-Rom interpolant of the table at u = |delta| / m (zero for u >= 1),
+// the table read through the read-only data cache.
+template <typename T>
+__device__ __forceinline__ T shannon_table_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
+    const int n = m - 1 - a;
+    const T delta = tau + static_cast<T>(n);
+    const T u = FM<T>::abs(delta) * wp.inv_m;
+    const bool centre = delta == T(0);
+    const T num = (n & 1) ? -s : s;
+    const T sc = centre ? T(1) : num * FM<T>::rcpw(static_cast<T>(kPiD) * delta);
+    const int tn = wp.table_n;
+    const T sx = u * static_cast<T>(tn);
+    int i = static_cast<int>(FM<T>::flr(sx));
+    i = min(max(i, 0), tn - 1);
+    const T t = sx - static_cast<T>(i);
+    if constexpr (sizeof(T) == 4) {
+        if (wp.tcoef) {   // one 16-byte load per weight
+            const float4 c = __ldg(wp.tcoef + i);
+            const T ph = fma(fma(fma(c.w, t, c.z), t, c.y), t, c.x);
+            return (u < T(1)) ? sc * ph : T(0);
+        }
+    }
+    const T* v = wp.table;
+    const T p1 = __ldg(v + i), p2 = __ldg(v + i + 1);
+    const T p0 = (i == 0) ? __ldg(v + 1) : __ldg(v + i - 1);
+    const T p3 = (i + 2 <= tn) ? __ldg(v + i + 2) : T(2) * __ldg(v + tn) - __ldg(v + tn - 1);
+    const T ph = T(0.5) * (T(2) * p1 + (p2 - p0) * t + (T(2) * p0 - T(5) * p1 + T(4) * p2 - p3) * t * t +
+                           (T(3) * p1 - p0 - T(3) * p2 + p3) * t * t * t);
+    return (u < T(1)) ? sc * ph : T(0);
+}
+
+template <typename T, int WK>
+__device__ __forceinline__ T shannon_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
+    return (WK == WK_TABLE) ? shannon_table_weight(tau, s, a, m, wp) : shannon_sinh_weight(tau, s, a, m, wp);
+}
+
 // The 2m tap weights psi_t(x - l/L) (Shannon) or phi_t(x - l/L) (classical)
-// of one dimension, tap a at l = i - m + 1 + a.  FAST = true is the
-// Shannon method with the sinh window (the default plan), evaluated inline
-// with no per-tap dispatch; the caller checks that the plan is of that kind.
-template <typename T, int W, bool FAST = false>
+// of one dimension, tap a at l = i - m + 1 + a.  WK = WK_SINH / WK_TABLE
+// evaluates the Shannon method with the sinh / tabulated window inline with
+// no per-tap dispatch; the caller checks that the plan is of that kind.
+template <typename T, int W, int WK = WK_GENERIC>
 __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w)[TapN<W>::A]) {
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
-    if (FAST) {
+    if (WK != WK_GENERIC) {
         const T s = FM<T>::sinpi(tau);
 #pragma unroll
         for (int a = 0; a < TapN<W>::A; ++a)
-            if (a < nw) w[a] = shannon_sinh_weight(tau, s, a, m, wp);
+            if (a < nw) w[a] = shannon_weight<T, WK>(tau, s, a, m, wp);
         return;
     }
     if (wp.method == NFFTBL_SHANNON) {
@@ -233,18 +285,22 @@ __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w
 // Write the 2m tap weights of two dimensions to d0[0 .. 2m-1] and
 // d1[0 .. 2m-1] (shared memory), the two dimensions' chains interleaved.
 template <typename T, int W>
-__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, bool fast, T tau0, T tau1, const WinParams<T>& wp);
+__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, int wk, T tau0, T tau1, const WinParams<T>& wp);
 
 // Write the 2m tap weights of one dimension to dst[0 .. 2m-1] (shared
 // memory), one at a time.
 template <typename T, int W>
-__device__ __forceinline__ void tap_weights_to(T* dst, bool fast, T tau, const WinParams<T>& wp) {
+__device__ __forceinline__ void tap_weights_to(T* dst, int wk, T tau, const WinParams<T>& wp) {
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
-    if (fast) {
+    if (wk == WK_SINH) {
         const T s = FM<T>::sinpi(tau);
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) dst[a] = shannon_sinh_weight(tau, s, a, m, wp);
+    } else if (wk == WK_TABLE) {
+        const T s = FM<T>::sinpi(tau);
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) dst[a] = shannon_table_weight(tau, s, a, m, wp);
     } else {
         T wt[TapN<W>::A];
         tap_weights<T, W>(tau, wp, wt);
@@ -255,10 +311,10 @@ __device__ __forceinline__ void tap_weights_to(T* dst, bool fast, T tau, const W
 }
 
 template <typename T, int W>
-__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, bool fast, T tau0, T tau1, const WinParams<T>& wp) {
-    if (!fast) {
-        tap_weights_to<T, W>(d0, false, tau0, wp);
-        tap_weights_to<T, W>(d1, false, tau1, wp);
+__device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, int wk, T tau0, T tau1, const WinParams<T>& wp) {
+    if (wk != WK_SINH) {
+        tap_weights_to<T, W>(d0, wk, tau0, wp);
+        tap_weights_to<T, W>(d1, wk, tau1, wp);
         return;
     }
     const int m = W ? W / 2 : wp.m;
@@ -499,12 +555,12 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
     }
 }
 
-// Contraction of one batch entry for the Shannon / sinh plan (d >= 2) with
+// Contraction of one batch entry for the Shannon / sinh or table plan (d >= 2) with
 // the dimension-0 weights evaluated inside the row loop: each is used once,
 // so they need no registers across the loop, and their SFU work overlaps
 // the rows' shared-memory loads and FMAs.  w1 (and w2) hold the other
 // dimensions' weights; s0 = sin(pi tau0).
-template <typename T, int D, int W>
+template <typename T, int D, int W, int WK>
 __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, const TileGeom& g, const int (&lb)[3],
                                                 T tau0, T s0, const T (&w1)[TapN<W>::A], const T (&w2)[TapN<W>::A],
                                                 const WinParams<T>& wp, int nw_rt) {
@@ -516,7 +572,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         const C2<T>* p = box + lb[0] * pitch + lb[1];
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) {
-            const T w0a = shannon_sinh_weight(tau0, s0, a, m, wp);
+            const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
             const C2<T>* row = p + a * pitch;
             T rr = T(0), ri = T(0);
 #pragma unroll
@@ -535,7 +591,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         const int p0 = g.box[1] * p1;
         const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
         for (int a = 0; a < nw; ++a) {
-            const T w0a = shannon_sinh_weight(tau0, s0, a, m, wp);
+            const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
             T mr = T(0), mi = T(0);
 #pragma unroll 2
             for (int b = 0; b < nw; ++b) {
@@ -566,14 +622,18 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
 // against the common path.
 template <typename T, int D, int W>
 __device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&lb)[3],
-                                                 const T (&tau)[3], bool fast, int b0, int nb, long long dst) {
+                                                 const T (&tau)[3], int wk, int b0, int nb, long long dst) {
     constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     T w0[A], w1[A], w2[A];
-    if (fast) {
-        tap_weights<T, W, true>(tau[0], a.w, w0);
-        if (D > 1) tap_weights<T, W, true>(tau[1], a.w, w1);
-        if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
+    if (wk == WK_SINH) {
+        tap_weights<T, W, WK_SINH>(tau[0], a.w, w0);
+        if (D > 1) tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
+    } else if (wk == WK_TABLE) {
+        tap_weights<T, W, WK_TABLE>(tau[0], a.w, w0);
+        if (D > 1) tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
     } else {
         tap_weights<T, W>(tau[0], a.w, w0);
         if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
@@ -670,7 +730,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
     __syncthreads();
     uint32_t phase = 0;
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
-    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
+    const int wk = weight_kind(a.w);
     constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     const int m = nw / 2;
@@ -690,15 +750,23 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 int lb[3] = {0, 0, 0};
                 node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
                 const long long dst = a.perm[i];
-                if (fast && D >= 2 && nb == 1 && a.comp == 0) {
+                if (wk == WK_SINH && D >= 2 && nb == 1 && a.comp == 0) {
                     T w1[A], w2[A];
-                    tap_weights<T, W, true>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W, true>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] =
-                        contract_lazy0<T, D, W>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_SINH>(
+                        box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
                     continue;
                 }
-                interp_node_general<T, D, W>(a, box, slot, lb, tau, fast, b0, nb, dst);
+                if (wk == WK_TABLE && D >= 2 && nb == 1 && a.comp == 0) {
+                    T w1[A], w2[A];
+                    tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_TABLE>(
+                        box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    continue;
+                }
+                interp_node_general<T, D, W>(a, box, slot, lb, tau, wk, b0, nb, dst);
             }
             __syncthreads();
         }
@@ -1123,7 +1191,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
     U* boxu = reinterpret_cast<U*>(smem + Ls.box);
     T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
     double* s_red = reinterpret_cast<double*>(smem + Ls.red);
-    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
+    const int wk = weight_kind(a.w);
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
@@ -1186,7 +1254,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             int lb[3] = {0, 0, 0};
                             node_setup_v<T, 2>(cx, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-                            tap_weights_to2<T, W>(row, row + A, fast, tau[0], tau[1], a.w);
+                            tap_weights_to2<T, W>(row, row + A, wk, tau[0], tau[1], a.w);
                             row[2 * A] = cg.x * inv_q;
                             row[2 * A + 1] = cg.y * inv_q;
                             reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
@@ -1302,7 +1370,7 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
     unsigned long long* boxz = reinterpret_cast<unsigned long long*>(smem + Ls.box);
     T* s_tab = reinterpret_cast<T*>(smem + Ls.w) + static_cast<size_t>(warp) * 32 * RS;
     double* s_red = reinterpret_cast<double*>(smem + Ls.red);
-    const bool fast = a.w.method == NFFTBL_SHANNON && a.w.window == NFFTBL_WIN_SINH;
+    const int wk = weight_kind(a.w);
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
         const WorkItem wi = a.work[item];
@@ -1332,7 +1400,7 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                             node_setup<T, 3>(a.xs, i, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
 #pragma unroll
-                            for (int t = 0; t < 3; ++t) tap_weights_to<T, W>(row + t * A, fast, tau[t], a.w);
+                            for (int t = 0; t < 3; ++t) tap_weights_to<T, W>(row + t * A, wk, tau[t], a.w);
                             const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
                             row[3 * A] = gv.x * inv_q;
                             row[3 * A + 1] = gv.y * inv_q;

@@ -136,9 +136,24 @@ __global__ void twiddle_kernel(int L, C2<T>* __restrict__ out) {
     out[j] = cmake<T>(static_cast<T>(c), static_cast<T>(s));
 }
 
-__global__ void table_cast_kernel(const double* __restrict__ in, int n, float* __restrict__ out) {
+// FP32 copy of the window table, and per interval i (of n - 1) the
+// Catmull-Rom cubic in t in [0, 1) as c0 + c1 t + c2 t^2 + c3 t^3 (ghost
+// values v_{-1} = v_1, v_n' = 2 v_{n-1} - v_{n-2} at the last sample),
+// formed in FP64 and rounded once.
+__global__ void table_cast_kernel(const double* __restrict__ in, int n, float* __restrict__ out,
+                                  float4* __restrict__ coef) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = static_cast<float>(in[i]);
+    const int tn = n - 1;
+    if (coef && i < tn) {
+        const double p0 = (i == 0) ? in[1] : in[i - 1];
+        const double p1 = in[i];
+        const double p2 = in[i + 1];
+        const double p3 = (i + 2 <= tn) ? in[i + 2] : 2.0 * in[tn] - in[tn - 1];
+        coef[i] = make_float4(static_cast<float>(p1), static_cast<float>(0.5 * (p2 - p0)),
+                              static_cast<float>(0.5 * (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3)),
+                              static_cast<float>(0.5 * (3.0 * p1 - p0 - 3.0 * p2 + p3)));
+    }
 }
 
 bool g_gl_uploaded = false;
@@ -215,8 +230,8 @@ cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_table_cast(const double* in, int n, float* out, cudaStream_t s) {
-    table_cast_kernel<<<(n + 255) / 256, 256, 0, s>>>(in, n, out);
+cudaError_t launch_table_cast(const double* in, int n, float* out, float4* coef, cudaStream_t s) {
+    table_cast_kernel<<<(n + 255) / 256, 256, 0, s>>>(in, n, out, coef);
     return cudaGetLastError();
 }
 
