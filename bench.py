@@ -111,6 +111,19 @@ def short_sum_roofline(d, m, N, B, M, seconds):
     return out
 
 
+def aggregate_over_ranks(t_step_ms, units_per_rank, world, device=None):
+    """Whole-job figures of N replicas: the step time is the maximum over the
+    ranks (every rank processes units_per_rank units per step), the value the
+    units of all ranks per second.  Returns (t_max_ms, value)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(t_step_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step_ms = float(tt.item())
+    return t_step_ms, world * units_per_rank / (t_step_ms * 1e-3)
+
+
 def run_unit_rates():
     """Build and run the unit-rate microbenchmark (FP32 FMA, ex2, rsqrt, rcp
     lane operations per SM per clock); prints one JSON line per unit."""
@@ -380,15 +393,12 @@ def run_ours(args, cfg):
     plan.sync()
     t_step = t_graph if t_graph is not None else t_stream
     launches = int(round(launches_per_step * args.steps))
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step, value = aggregate_over_ranks(t_step, N, world, dev)
     launch_mode = "CUDA graph replay of the captured forward + adjoint calls" if graph is not None else "stream launches"
     if args.quick:
         # timed region only (used for profiling captures): no comparison legs
         if rank == 0:
-            print(json.dumps({"quick": True, "config": cfg, "ms_per_step": t_step, "value": world * N / (t_step * 1e-3),
+            print(json.dumps({"quick": True, "config": cfg, "ms_per_step": t_step, "value": value,
                               "unit": UNIT, "gpu_launches": launches, "clocks": clk,
                               "set_nodes_ms": float(np.median(set_ms)), "stream_ms_per_step": t_stream,
                               "launch": launch_mode,
@@ -491,7 +501,6 @@ def run_ours(args, cfg):
         n_sample = min(n_sample, N)
         cb = run_oracle_sample(cfg, x, fh, g, plan.beta, n_sample, f_gpu=f32.cpu().numpy())
         cpu_value = cb["n"] / cb["seconds"]
-        value = world * N / (t_step * 1e-3)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",

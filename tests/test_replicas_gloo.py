@@ -1,0 +1,60 @@
+"""The multi-GPU mode of bench.py is N independent replicas of the workload
+(the transform does not shard on a one-GPU pool): the whole-job step time is
+the maximum over the ranks and the value counts the units of every rank.
+These tests run that host logic as two `gloo` ranks on CPU, and check that
+the reference arm leaves ranks other than 0 without work."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+_RANK_CHILD = r"""
+import json, os, sys
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+dist.init_process_group("gloo")
+import bench
+rank, world = dist.get_rank(), dist.get_world_size()
+t, v = bench.aggregate_over_ranks(1.0 + rank, 1000, world, "cpu")
+print(json.dumps({"rank": rank, "t": t, "value": v}))
+dist.destroy_process_group()
+"""
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_replicas_take_max_time_and_count_all_units():
+    pytest.importorskip("torch")
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port), CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, "-c", _RANK_CHILD, ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=180)
+        assert p.returncode == 0, err[-2000:]
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for r in outs:
+        # rank 0 took 1 ms, rank 1 took 2 ms: the job's step is 2 ms for 2 x 1000 units
+        assert r["t"] == 2.0
+        assert r["value"] == pytest.approx(2 * 1000 / 2e-3)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "3", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr[-2000:]
+    assert res.stdout.strip() == ""
