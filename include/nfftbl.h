@@ -87,6 +87,11 @@ typedef struct {
     int table_len;          /* >= 3 for NFFTBL_WIN_TABLE                                  */
     int tile[3];            /* node-binning tile shape in grid cells; 0 = default         */
     int nodes_per_item;     /* nodes per (tile, chunk) work item, <= 2047; 0 = default 1024 */
+    int factors;            /* step 0b of Algorithm 4.2 in tensor-product form: 1 keeps the
+                               d x 2m window factors of every node, computed once by
+                               nfftbl_set_nodes (N * d * 2m values in the plan precision,
+                               rows padded to 4); 0 (default) evaluates them in every
+                               transform, which is faster on GB300 for the sinh window  */
 } nfftbl_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -106,6 +106,12 @@ nfftbl_status make_tmap(nfftbl_plan_s* p) {
     return NFFTBL_OK;
 }
 
+// Row length of the stored window factors: d * 2m rounded up to a multiple
+// of 4 (rows start 16-byte aligned).
+int factor_stride(const nfftbl_plan_s* p) {
+    return (p->d * 2 * p->m + 3) / 4 * 4;
+}
+
 template <typename T>
 TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
     TapArgs<T> a{};
@@ -124,6 +130,8 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
         a.w.c_norm = T(1);
     a.w.table = static_cast<const T*>(p->window == NFFTBL_WIN_TABLE ? p->table_dev.p : nullptr);
     a.w.table_n = static_cast<int>(p->table_host.size()) - 1;
+    a.wstride = factor_stride(p);
+    a.wfac = p->wfac_valid ? static_cast<const T*>(p->wfac.p) : nullptr;
     a.w.tcoef = (sizeof(T) == 4 && p->window == NFFTBL_WIN_TABLE) ? static_cast<const float4*>(p->table_coef.p) : nullptr;
     a.batch = p->batch;
     const size_t bb = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
@@ -235,6 +243,7 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->keys_tmp);
     free_buf(p->perm_tmp);
     free_buf(p->hist);
+    free_buf(p->wfac);
     free_buf(p->table_coef);
     free_buf(p->scan_tmp);
     free_buf(p->tile_off);
@@ -342,6 +351,7 @@ void nfftbl_default_opts(nfftbl_opts* o) {
     o->method = NFFTBL_SHANNON;
     o->beta = 0.0;
     o->batch = 1;
+    o->factors = 0;
 }
 
 nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m, int window,
@@ -359,6 +369,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     if (window < 0 || window > 2) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown window");
     if (o.precision < 0 || o.precision > 2) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown precision");
     if (o.method < 0 || o.method > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown method");
+    if (o.factors < 0 || o.factors > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "factors must be 0 or 1");
     if (o.batch < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "batch must be >= 1");
     if (window == NFFTBL_WIN_TABLE && (!o.table || o.table_len < 3))
         return plan_fail(nullptr, NFFTBL_EINVAL, "table window needs a table of >= 3 values");
@@ -435,6 +446,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     p->beta = beta;
     p->batch = o.batch;
     p->nodes_per_item = o.nodes_per_item > 0 ? o.nodes_per_item : 1024;
+    p->store_factors = o.factors;
     p->geom = g;
     p->smem_optin = optin;
     p->key_bits = key_bits;
@@ -522,12 +534,38 @@ nfftbl_status nfftbl_set_stream(nfftbl_plan_t p, void* stream) {
     return NFFTBL_OK;
 }
 
+// Step 0b (tensor-product form): the d x 2m window factors of every sorted
+// node, kept for the transforms.  Without memory for them the transforms
+// evaluate the factors themselves (no error).
+static nfftbl_status compute_factors(nfftbl_plan_t p) {
+    p->wfac_valid = false;
+    if (!p->store_factors || p->N <= 0) return NFFTBL_OK;
+    const size_t es = (p->precision == NFFTBL_F64) ? sizeof(double) : sizeof(float);
+    const size_t bytes = static_cast<size_t>(p->N) * factor_stride(p) * es;
+    if (p->wfac.bytes < bytes) {
+        free_buf(p->wfac);
+        void* ptr = nullptr;
+        if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return NFFTBL_OK;
+        }
+        p->wfac.p = ptr;
+        p->wfac.bytes = bytes;
+    }
+    nfftbl_status st = taps(p, TAP_FACTORS, nullptr, nullptr, nullptr);
+    if (st == NFFTBL_OK) p->wfac_valid = true;
+    return st;
+}
+
 nfftbl_status nfftbl_set_nodes(nfftbl_plan_t p, int64_t N, const void* x_dev) {
     if (!p) return NFFTBL_EINVAL;
     if (N < 0 || N >= (1LL << 31)) return fail(p, NFFTBL_EINVAL, "N must be in [0, 2^31)");
     if (N > 0 && !x_dev) return fail(p, NFFTBL_EINVAL, "x_dev is NULL");
     p->last_error.clear();
-    return bin_nodes(p, N, x_dev);
+    p->wfac_valid = false;
+    nfftbl_status st = bin_nodes(p, N, x_dev);
+    if (st != NFFTBL_OK) return st;
+    return compute_factors(p);
 }
 
 static nfftbl_status ready(nfftbl_plan_t p) {
@@ -701,6 +739,8 @@ nfftbl_status nfftbl_set_window_table(nfftbl_plan_t p, const double* table_dev, 
             return st;
         p->launches += 2;
     }
+    // stored factors follow the new table
+    if (p->wfac_valid) return compute_factors(p);
     return NFFTBL_OK;
 }
 

@@ -64,6 +64,8 @@ struct TapArgs {
     int spread_batch;          // batch entries per shared-memory box group
     T wbound;                  // bound on prod_t |window factor| (1 for sinh / cKB)
     int spread_warps;          // warps per block of the d = 3 spread kernel
+    const T* wfac;             // stored window factors (sorted node i: row i of wstride), or null
+    int wstride;               // row length of wfac: d * 2m rounded up to a multiple of 4
 };
 
 // Shared-memory layout of spread_kernel (byte offsets), shared with the host.
@@ -202,6 +204,9 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf keys, perm;         // sorted keys / permutation (uint32)
     nfftbl::DeviceBuf keys_tmp, perm_tmp; // radix sort ping-pong
     nfftbl::DeviceBuf hist;               // radix sort block histograms
+    nfftbl::DeviceBuf wfac;               // stored window factors (step 0b, tensor-product form)
+    int store_factors = 1;
+    bool wfac_valid = false;
     nfftbl::DeviceBuf table_coef;         // FP32 table window: float4 cubic coefficients per interval
     nfftbl::DeviceBuf scan_tmp;           // per-tile sums of the multi-block scan
     nfftbl::DeviceBuf tile_off;           // n_tiles + 1 (uint32)
@@ -273,7 +278,7 @@ cudaError_t launch_fft_forward_pass_f32(const void* in, void* out, long long out
 // Short-sum kernels (taps.cuh).  launch_tap_kernel is instantiated once per
 // (precision, dimension, tap count W = 2m, or W = 0 for m read at run time)
 // in translation units the build generates; taps_dispatch.cu picks one.
-enum TapKind { TAP_INTERP = 0, TAP_SPREAD = 1, TAP_GRAD = 2 };
+enum TapKind { TAP_INTERP = 0, TAP_SPREAD = 1, TAP_GRAD = 2, TAP_FACTORS = 3 };
 template <typename T, int D, int W>
 nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem);
 template <typename T, int D>

@@ -615,18 +615,66 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
     return cmake<T>(ar, ai);
 }
 
+// Copy n = 2m (n <= A) window factors from src to dst with the widest
+// aligned vector accesses the compile-time tap count allows (the stored
+// rows and their per-dimension parts start 16-byte aligned when 2m is a
+// multiple of 4 floats / 2 doubles).
+template <typename T, int W, typename Dst>
+__device__ __forceinline__ void load_factors(const T* __restrict__ src, Dst& dst, int n) {
+    constexpr int A = TapN<W>::A;
+    if (W != 0 && sizeof(T) == 4 && W % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < A; q += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src + q));
+            dst[q] = v.x; dst[q + 1] = v.y; dst[q + 2] = v.z; dst[q + 3] = v.w;
+        }
+    } else if (W != 0 && W % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < A; q += 2) {
+            if (sizeof(T) == 4) {
+                const float2 v = __ldg(reinterpret_cast<const float2*>(src + q));
+                dst[q] = v.x; dst[q + 1] = v.y;
+            } else {
+                const double2 v = __ldg(reinterpret_cast<const double2*>(src + q));
+                dst[q] = v.x; dst[q + 1] = v.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < A; ++q)
+            if (q < n) dst[q] = __ldg(src + q);
+    }
+}
+
+// Copy the stored factors of one node (D dimensions of n = 2m each) into a
+// node-table row whose dimension t starts at t * A.  Out of line: only plans
+// with stored factors take it.
+template <typename T, int W>
+__device__ __noinline__ void copy_factor_rows(const T* __restrict__ src, T* dst, int D, int n) {
+    for (int t = 0; t < D; ++t) {
+        T* d = dst + t * TapN<W>::A;
+        load_factors<T, W>(src + t * n, d, n);
+    }
+}
+
 // One node of interp_kernel for every plan other than the single-batch
-// Shannon / sinh case (other windows, the classical method, batches,
-// compensated sums): all weights in registers, then one contraction per
-// batch entry.  Kept out of line so that its registers do not count
+// Shannon / sinh or table case (other windows, the classical method,
+// batches, compensated sums, stored factors): all weights in registers, then
+// one contraction per batch entry.  Kept out of line so that its registers do not count
 // against the common path.
 template <typename T, int D, int W>
 __device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&lb)[3],
-                                                 const T (&tau)[3], int wk, int b0, int nb, long long dst) {
+                                                 const T (&tau)[3], int wk, int b0, int nb, long long i,
+                                                 long long dst) {
     constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     T w0[A], w1[A], w2[A];
-    if (wk == WK_SINH) {
+    if (a.wfac) {   // stored factors (step 0b)
+        const T* wr = a.wfac + i * a.wstride;
+        load_factors<T, W>(wr, w0, nw);
+        if (D > 1) load_factors<T, W>(wr + nw, w1, nw);
+        if (D > 2) load_factors<T, W>(wr + 2 * nw, w2, nw);
+    } else if (wk == WK_SINH) {
         tap_weights<T, W, WK_SINH>(tau[0], a.w, w0);
         if (D > 1) tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
         if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
@@ -711,6 +759,36 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap* tmap, const TapArgs
     return true;
 }
 
+// Step 0b of Algorithm 4.2 in tensor-product form: the 2m window factors of
+// every dimension of every sorted node, row i = [dim 0 | dim 1 | dim 2]
+// (each 2m long) padded to wstride; the same arithmetic as the transforms'
+// own evaluation.
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(256) factor_kernel(const TapArgs<T> a, T* __restrict__ out) {
+    constexpr int A = TapN<W>::A;
+    const int nw = W ? W : 2 * a.w.m;
+    const int wk = weight_kind(a.w);
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < a.N;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        T* row = out + i * a.wstride;
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            const T u = mul_rn(static_cast<T>(a.g.L[t]), a.xs[i * D + t]);
+            const T tau = u - FM<T>::flr(u);
+            T w[A];
+            if (wk == WK_SINH)
+                tap_weights<T, W, WK_SINH>(tau, a.w, w);
+            else if (wk == WK_TABLE)
+                tap_weights<T, W, WK_TABLE>(tau, a.w, w);
+            else
+                tap_weights<T, W>(tau, a.w, w);
+#pragma unroll
+            for (int q = 0; q < A; ++q)
+                if (q < nw) row[t * nw + q] = w[q];
+        }
+    }
+}
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const TapArgs<T> a) {
@@ -750,7 +828,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 int lb[3] = {0, 0, 0};
                 node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
                 const long long dst = a.perm[i];
-                if (wk == WK_SINH && D >= 2 && nb == 1 && a.comp == 0) {
+                if (!a.wfac && wk == WK_SINH && D >= 2 && nb == 1 && a.comp == 0) {
                     T w1[A], w2[A];
                     tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
@@ -758,7 +836,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                         box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
                     continue;
                 }
-                if (wk == WK_TABLE && D >= 2 && nb == 1 && a.comp == 0) {
+                if (!a.wfac && wk == WK_TABLE && D >= 2 && nb == 1 && a.comp == 0) {
                     T w1[A], w2[A];
                     tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
@@ -766,7 +844,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                         box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
                     continue;
                 }
-                interp_node_general<T, D, W>(a, box, slot, lb, tau, wk, b0, nb, dst);
+                interp_node_general<T, D, W>(a, box, slot, lb, tau, wk, b0, nb, i, dst);
             }
             __syncthreads();
         }
@@ -1254,7 +1332,12 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             int lb[3] = {0, 0, 0};
                             node_setup_v<T, 2>(cx, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-                            tap_weights_to2<T, W>(row, row + A, wk, tau[0], tau[1], a.w);
+                            if (a.wfac) {   // stored factors (step 0b)
+                                copy_factor_rows<T, W>(a.wfac + (static_cast<long long>(wi.start) + c0 + lane) * a.wstride,
+                                                       row, 2, nw);
+                            } else {
+                                tap_weights_to2<T, W>(row, row + A, wk, tau[0], tau[1], a.w);
+                            }
                             row[2 * A] = cg.x * inv_q;
                             row[2 * A + 1] = cg.y * inv_q;
                             reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
@@ -1400,7 +1483,12 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                             node_setup<T, 3>(a.xs, i, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
 #pragma unroll
-                            for (int t = 0; t < 3; ++t) tap_weights_to<T, W>(row + t * A, wk, tau[t], a.w);
+                            if (a.wfac) {   // stored factors (step 0b)
+                                copy_factor_rows<T, W>(a.wfac + i * a.wstride, row, 3, nw);
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < 3; ++t) tap_weights_to<T, W>(row + t * A, wk, tau[t], a.w);
+                            }
                             const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + a.perm[i]];
                             row[3 * A] = gv.x * inv_q;
                             row[3 * A + 1] = gv.y * inv_q;
@@ -1624,6 +1712,18 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
                         : reinterpret_cast<void*>(spread_kernel<T, D, W>);
     const int threads = (kind == TAP_SPREAD && D == 3) ? 32 * args.spread_warps : kTapThreads;
     if (kind == TAP_GRAD) fn = reinterpret_cast<void*>(node_grad_kernel<T, D, W>);
+    if (kind == TAP_FACTORS) {
+        if (args.N <= 0) return NFFTBL_OK;
+        int occf = 0;
+        nfftbl_status stf = check_cuda(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                              &occf, factor_kernel<T, D, W>, 256, 0), "occupancy");
+        if (stf != NFFTBL_OK) return stf;
+        const long long wantf = static_cast<long long>(std::max(occf, 1)) * p->num_sms;
+        const unsigned gridf = static_cast<unsigned>(std::min<long long>(wantf, (args.N + 255) / 256));
+        factor_kernel<T, D, W><<<gridf, 256, 0, p->stream>>>(args, static_cast<T*>(p->wfac.p));
+        p->launches++;
+        return check_cuda(p, cudaGetLastError(), "factor kernel launch");
+    }
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           static_cast<int>(smem)),
                                   "tap smem attribute");

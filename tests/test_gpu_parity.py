@@ -38,13 +38,13 @@ def built():
 
 
 def make(d, prec, method="shannon", window="sinh", batch=1, m=None, M=None, N=None, table=None, seed=0,
-         npi=None):
+         npi=None, factors=False):
     M0, m0, N0, npi0 = SHAPES[d]
     M = M or M0
     m = m or m0
     N = N if N is not None else N0
     plan = nb.Plan(d, M, 2.0, m, window=window, precision=prec, method=method, batch=batch, table=table,
-                   nodes_per_item=npi or npi0)
+                   nodes_per_item=npi or npi0, factors=factors)
     x = W.nodes_uniform(N, d, seed=seed, dtype=RDT[prec])
     plan.set_nodes(to_dev(x))
     return plan, x
@@ -133,6 +133,35 @@ def test_adjoint_parity(d, prec, method):
     plan.sync()
     ref = O.adjoint(oracle_plan(plan), g, x)
     assert rel_l2(fh, ref) < TOL[prec]
+
+
+FACTOR_CASES = [(d, prec, method, window) for d in (1, 2, 3) for prec in ("f64", "f32")
+                for method, window in (("shannon", "sinh"), ("classic", "sinh"), ("shannon", "table"),
+                                       ("shannon", "ckb"))]
+
+
+@pytest.mark.parametrize("d,prec,method,window", FACTOR_CASES)
+def test_stored_factors_match_evaluated(d, prec, method, window):
+    """Step 0b in tensor-product form: with the window factors stored by
+    set_nodes (factors=True) and evaluated in every transform (default),
+    forward and adjoint agree with the oracle, and with each other to the
+    rounding of the plan precision."""
+    batch = 2
+    table = O.learned_table(O.mlp_init()) if window == "table" else None
+    outs = {}
+    for factors in (True, False):
+        plan, x = make(d, prec, method=method, window=window, batch=batch, table=table, factors=factors)
+        fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+        g = W.adjoint_input(x.shape[0], batch=batch, dtype=CDT[prec])
+        outs[factors] = (to_host(plan.forward(to_dev(fh))), to_host(plan.adjoint(to_dev(g))))
+        plan.sync()
+    op = oracle_plan(plan, table=table)
+    for factors in (True, False):
+        assert rel_l2(outs[factors][0], O.forward(op, fh, x)) < TOL[prec]
+        assert rel_l2(outs[factors][1], O.adjoint(op, g, x)) < TOL[prec]
+    agree = 1e-14 if prec == "f64" else 1e-6
+    assert rel_l2(outs[True][0], outs[False][0]) < agree
+    assert rel_l2(outs[True][1], outs[False][1]) < agree
 
 
 @pytest.mark.parametrize("d", [1, 2, 3])
