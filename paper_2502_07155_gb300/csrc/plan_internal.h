@@ -68,10 +68,15 @@ struct TapArgs {
     int wstride;               // row length of wfac: d * 2m rounded up to a multiple of 4
 };
 
-// Shared-memory layout of spread_kernel (byte offsets), shared with the host.
+// Shared-memory layout of the spread kernels (byte offsets), shared with the host.
 struct SpreadSmem {
     size_t box, lb, w, g, run, red, total;
 };
+
+// Reduction scratch of every spread kernel, in doubles: [0, 32) per-warp
+// sums, 32 and 33 the item's quantum and flag, 36 .. 39 the quantum
+// constants in the plan precision (see item_quantum).
+constexpr int kSpreadRedDoubles = 40;
 
 template <typename T>
 __host__ __device__ __forceinline__ SpreadSmem spread_smem_layout(int d, int A, int box_cells, int nb, int sub) {
@@ -84,7 +89,7 @@ __host__ __device__ __forceinline__ SpreadSmem spread_smem_layout(int d, int A, 
     L.g = al(L.w + static_cast<size_t>(sub) * d * A * sizeof(T));
     L.run = al(L.g + static_cast<size_t>(nb) * sub * 2 * sizeof(T));
     L.red = al(L.run + static_cast<size_t>(sub + 1) * 4);
-    L.total = al(L.red + 34 * 8);
+    L.total = al(L.red + kSpreadRedDoubles * 8);
     return L;
 }
 
@@ -108,7 +113,7 @@ __host__ __device__ __forceinline__ SpreadSmem spread2_layout(int A, int box_cel
     L.w = al(L.box + static_cast<size_t>(nb) * slot * 16);
     L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread2_row<T>(A) * sizeof(T));
     L.lb = L.g = L.run = L.red;
-    L.total = al(L.red + 40 * 8);
+    L.total = al(L.red + kSpreadRedDoubles * 8);
     return L;
 }
 
@@ -128,7 +133,7 @@ __host__ __device__ __forceinline__ SpreadSmem spread3_layout(int A, int box_cel
     L.w = al(L.box + static_cast<size_t>(nb) * box_cells * 16);
     L.red = al(L.w + static_cast<size_t>(nwarps) * 32 * spread3_row<T>(A) * sizeof(T));
     L.lb = L.g = L.run = L.red;
-    L.total = al(L.red + 40 * 8);
+    L.total = al(L.red + kSpreadRedDoubles * 8);
     return L;
 }
 

@@ -854,267 +854,20 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // Spreading (transposed short sums, the Psi^T factor of the adjoint).
 //
-// Exact accumulation: a work item's box is accumulated in 64-bit fixed
-// point in shared memory with a power-of-two quantum q = 2^(e - 62), where
-// 2^e bounds the item's total |g| times the largest product of window
-// values, so no partial sum can overflow.  Integer addition is associative,
-// so the box is exact and independent of the order in which warps add.
-//
-// Work split: nodes are sorted by cell, so runs of consecutive nodes share
-// their 2m^d taps.  A warp takes one run; lane l owns the contiguous-
-// dimension tap c = l mod 2m and a set of rows (row group l div 2m); it sums
-// the run's contributions for its taps in registers and adds each sum to
-// the box once.
+// Exact accumulation: a work item's box is accumulated in fixed point in
+// shared memory with a power-of-two quantum chosen from a bound on the
+// item's total contribution (FixedCell below), so no partial sum can
+// overflow.  Integer addition is associative, so the box is exact and
+// independent of the order in which warps add.
 //
 // Ordered flush: the item's box (converted back to the plan's precision)
 // is stored to its own slot of a scratch array; gather_kernel then forms
 // every grid value as the sum over the boxes that cover it in a fixed
 // order (tiles in row-major order, then the tile's items in order).  No
 // global atomics, no clearing of the grid, bitwise reproducible results.
-
-template <typename T> __device__ __forceinline__ long long to_fixed(T v, T inv_q);
-template <> __device__ __forceinline__ long long to_fixed<float>(float v, float inv_q) {
-    return __float2ll_rn(v * inv_q);
-}
-template <> __device__ __forceinline__ long long to_fixed<double>(double v, double inv_q) {
-    return __double2ll_rn(v * inv_q);
-}
-
-__device__ __forceinline__ void fixed_add(unsigned long long* p, long long v) {
-    if (v != 0) atomicAdd(p, static_cast<unsigned long long>(v));
-}
-
-template <typename T, int D, int W>
-__global__ void __launch_bounds__(kTapThreads) spread_kernel(const TapArgs<T> a) {
-    using CT = C2<T>;
-    using U = unsigned long long;
-    constexpr int A = TapN<W>::A;
-    const int nw = W ? W : 2 * a.w.m;
-    const int m = nw / 2;
-    extern __shared__ __align__(128) unsigned char smem[];
-    int box_cells = 1;
-#pragma unroll
-    for (int t = 0; t < D; ++t) box_cells *= a.g.box[t];
-    const int slot = (box_cells + 1) / 2 * 2;
-    const int nbmax = a.spread_batch;
-    const int sub = a.spread_sub;
-    const SpreadSmem L = spread_smem_layout<T>(D, A, box_cells, nbmax, sub);
-    U* boxu = reinterpret_cast<U*>(smem + L.box);
-    int* s_lb = reinterpret_cast<int*>(smem + L.lb);
-    T* s_w = reinterpret_cast<T*>(smem + L.w);
-    CT* s_g = reinterpret_cast<CT*>(smem + L.g);
-    int* s_run = reinterpret_cast<int*>(smem + L.run);
-    double* s_red = reinterpret_cast<double*>(smem + L.red);
-    const bool periodic = a.w.method == NFFTBL_CLASSIC;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int G = 32 / nw;                       // row groups per warp
-    const int c = lane % nw;                     // owned contiguous-dimension tap
-    const int rg = lane / nw;                    // row group
-    const bool active = rg < G;
-
-    for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
-        const WorkItem wi = a.work[item];
-        int org[3] = {0, 0, 0};
-        tile_origin<D>(a.g, wi.tile, periodic, org);
-        for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
-            const int nb = min(nbmax, a.batch - b0);
-            // ---- quantum: bound on the item's total contribution
-            double part = 0.0;
-            for (int j = tid; j < wi.count; j += blockDim.x) {
-                const long long src = a.perm[wi.start + j];
-                for (int bb = 0; bb < nb; ++bb) {
-                    const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-                    part += fabs(static_cast<double>(gv.x)) + fabs(static_cast<double>(gv.y));
-                }
-            }
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(0xffffffffu, part, off);
-            if (lane == 0) s_red[warp] = part;
-            for (int idx = tid; idx < nb * slot * 2; idx += blockDim.x) boxu[idx] = 0ull;
-            __syncthreads();
-            if (tid == 0) {
-                double tot = 0.0;
-                for (int w = 0; w < nwarps; ++w) tot += s_red[w];
-                tot *= static_cast<double>(a.wbound) * 1.0001;
-                int e = 0;
-                if (tot > 0.0) e = max(ilogb(tot) + 1, -60);   // tot < 2^e; 2^(62-e) stays a finite float
-                s_red[32] = ldexp(1.0, e - 62);                // quantum q
-                s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
-            }
-            __syncthreads();
-            const double qd = s_red[32];
-            const bool any = s_red[33] != 0.0;
-            const T inv_q = static_cast<T>(1.0 / qd);
-            if (any) {
-                for (int s0 = 0; s0 < wi.count; s0 += sub) {
-                    const int ns = min(sub, wi.count - s0);
-                    // ---- per-node setup: local first tap, window factors, inputs
-                    if (tid < ns) {
-                        const long long i = static_cast<long long>(wi.start) + s0 + tid;
-                        T tau[3];
-                        int lb[3] = {0, 0, 0};
-                        node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
-                        s_lb[tid] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
-                        T wt[A];
-#pragma unroll
-                        for (int t = 0; t < D; ++t) {
-                            tap_weights<T, W>(tau[t], a.w, wt);
-                            T* dst = s_w + (static_cast<size_t>(tid) * D + t) * A;
-#pragma unroll
-                            for (int q = 0; q < nw; ++q) dst[q] = wt[q];
-                        }
-                        const long long src = a.perm[i];
-                        for (int bb = 0; bb < nb; ++bb)
-                            s_g[bb * sub + tid] = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
-                    }
-                    __syncthreads();
-                    // ---- groups of consecutive (cell-sorted) nodes: for d = 1 the nodes of
-                    // one cell; for d >= 2 the nodes of one box row (same leading taps)
-                    // whose contiguous-dimension first tap lies in one segment of S cells,
-                    // so that the group's taps span at most 32 columns (one per lane)
-                    const int S = 33 - nw;
-                    int nruns = 0;
-                    {
-                        auto key = [&](int j) -> int {
-                            const int lbp = s_lb[j];
-                            if (D != 2) return lbp;
-                            const int fast = (D == 2) ? ((lbp >> 10) & 1023) : (lbp >> 20);
-                            const int lead = (D == 2) ? (lbp & 1023) : (lbp & 0xFFFFF);
-                            return lead | ((fast / S) << 20);
-                        };
-                        const int flag = (tid < ns) && (tid == 0 || key(tid) != key(tid - 1));
-                        const unsigned bal = __ballot_sync(0xffffffffu, flag);
-                        const int before = __popc(bal & ((1u << lane) - 1u));
-                        if (lane == 0) s_red[warp] = __popc(bal);
-                        __syncthreads();
-                        int wbase = 0;
-                        for (int w = 0; w < warp; ++w) wbase += static_cast<int>(s_red[w]);
-                        for (int w = 0; w < nwarps; ++w) nruns += static_cast<int>(s_red[w]);
-                        if (flag) s_run[wbase + before] = tid;
-                        if (tid == 0) s_run[nruns] = ns;
-                        __syncthreads();
-                    }
-                    if (D == 1) {
-                        // lanes own taps; row groups split the run's nodes (sums are exact)
-                        if (active) {
-                            for (int r = warp; r < nruns; r += nwarps) {
-                                const int jlo = s_run[r], jhi = s_run[r + 1];
-                                const int lb0 = s_lb[jlo] & 1023;
-                                for (int bb = 0; bb < nb; ++bb) {
-                                    U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
-                                    const CT* gg = s_g + bb * sub;
-                                    T ar = T(0), ai = T(0);
-                                    for (int j = jlo + rg; j < jhi; j += G) {
-                                        const T wv = s_w[static_cast<size_t>(j) * A + c];
-                                        ar += gg[j].x * wv;
-                                        ai += gg[j].y * wv;
-                                    }
-                                    const int cell = lb0 + c;
-                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar, inv_q));
-                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai, inv_q));
-                                }
-                            }
-                        }
-                    } else {
-                        // lanes own absolute box columns; each sums its column's
-                        // contributions over the group for all 2m rows in registers
-                        for (int r = warp; r < nruns; r += nwarps) {
-                            const int jlo = s_run[r], jhi = s_run[r + 1];
-                            const int lbp = s_lb[jlo];
-                            const int lb0 = lbp & 1023, lb1 = (lbp >> 10) & 1023;
-                            const int fast0 = (((D == 2) ? lb1 : (lbp >> 20)) / S) * S;
-                            const int col = fast0 + lane;
-                            const bool live = col < a.g.box[D - 1];
-                            for (int bb = 0; bb < nb; ++bb) {
-                                U* bx = boxu + static_cast<size_t>(bb) * slot * 2;
-                                const CT* gg = s_g + bb * sub;
-                                if (D == 2) {
-                                    T ar[A], ai[A];
-#pragma unroll
-                                    for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
-                                    for (int j = jlo; j < jhi; ++j) {
-                                        const T* wj = s_w + static_cast<size_t>(j) * 2 * A;
-                                        const int t = col - ((s_lb[j] >> 10) & 1023);
-                                        const bool in = (t >= 0) && (t < nw);
-                                        const T wf = in ? wj[A + (in ? t : 0)] : T(0);
-                                        const CT gv = gg[j];
-                                        const T gr = gv.x * wf, gi = gv.y * wf;
-                                        T w0r[A];
-                                        load_row<T, A>(wj, w0r);
-#pragma unroll
-                                        for (int q = 0; q < A; ++q) {
-                                            if (q < nw) {
-                                                ar[q] += gr * w0r[q];
-                                                ai[q] += gi * w0r[q];
-                                            }
-                                        }
-                                    }
-                                    if (live) {
-                                        const int pitch = a.g.box[1];
-#pragma unroll
-                                        for (int q = 0; q < A; ++q) {
-                                            if (q < nw) {
-                                                const int cell = (lb0 + q) * pitch + col;
-                                                fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
-                                                fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
-                                            }
-                                        }
-                                    }
-                                } else {
-                                    const int p2 = a.g.box[2];
-                                    const int p1 = a.g.box[1] * p2;
-                                    for (int a0 = 0; a0 < nw; ++a0) {
-                                        T ar[A], ai[A];
-#pragma unroll
-                                        for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
-                                        for (int j = jlo; j < jhi; ++j) {
-                                            const T* wj = s_w + static_cast<size_t>(j) * 3 * A;
-                                            const int t = col - (s_lb[j] >> 20);
-                                            const bool in = (t >= 0) && (t < nw);
-                                            const T wf = in ? wj[2 * A + (in ? t : 0)] * wj[a0] : T(0);
-                                            const CT gv = gg[j];
-                                            const T gr = gv.x * wf, gi = gv.y * wf;
-                                            T w1r[A];
-                                            load_row<T, A>(wj + A, w1r);
-#pragma unroll
-                                            for (int q = 0; q < A; ++q) {
-                                                if (q < nw) {
-                                                    ar[q] += gr * w1r[q];
-                                                    ai[q] += gi * w1r[q];
-                                                }
-                                            }
-                                        }
-                                        if (live) {
-#pragma unroll
-                                            for (int q = 0; q < A; ++q) {
-                                                if (q < nw) {
-                                                    const int cell = (lb0 + a0) * p1 + (lb1 + q) * p2 + col;
-                                                    fixed_add(bx + 2 * cell, to_fixed<T>(ar[q], inv_q));
-                                                    fixed_add(bx + 2 * cell + 1, to_fixed<T>(ai[q], inv_q));
-                                                }
-                                            }
-                                        }
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-            // ---- store the item's box (plan precision) to its scratch slot
-            for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
-                const int bb = idx / box_cells;
-                const int cell = idx - bb * box_cells;
-                const U* u = boxu + (static_cast<size_t>(bb) * slot + cell) * 2;
-                CT v;
-                v.x = static_cast<T>(static_cast<double>(static_cast<long long>(u[0])) * qd);
-                v.y = static_cast<T>(static_cast<double>(static_cast<long long>(u[1])) * qd);
-                a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
-            }
-            __syncthreads();
-        }
-    }
-}
+//
+// Kernels: spread1_kernel (d = 1), spread2_kernel (d = 2), spread3_kernel
+// (d = 3).
 
 // Fixed-point cells of the d = 2 / d = 3 spreading boxes (16 bytes per cell).
 //  FP32: each component holds v = hi * 2^21 + lo in two int32 words, with
@@ -1216,6 +969,7 @@ __device__ __forceinline__ void item_quantum(const TapArgs<T>& a, int nwarps, do
     s_red[32] = ldexp(1.0, e - FixedCell<T>::kBits);
     s_red[33] = (tot > 0.0) ? 1.0 : 0.0;
     // the same powers of two in the plan precision: 1/q, q, q 2^21, flag
+    static_assert(kSpreadRedDoubles * 8 >= 36 * 8 + 4 * sizeof(T), "reduction scratch too small");
     T* f = reinterpret_cast<T*>(s_red + 36);
     f[0] = static_cast<T>(ldexp(1.0, FixedCell<T>::kBits - e));
     f[1] = static_cast<T>(s_red[32]);
@@ -1553,6 +1307,112 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
     }
 }
 
+// d = 1 spreading.  Nodes are staged `sub` at a time (weights and the
+// pre-scaled inputs in shared memory); runs of nodes in one cell share their
+// 2m taps.  A warp takes a run: lane l owns tap c = l mod 2m and row group
+// l div 2m, the row groups split the run's nodes, and every lane adds its
+// partial sum to the box once (exact integer adds).
+template <typename T, int W>
+__global__ void __launch_bounds__(kTapThreads) spread1_kernel(const TapArgs<T> a) {
+    using CT = C2<T>;
+    constexpr int A = TapN<W>::A;
+    const int nw = W ? W : 2 * a.w.m;
+    const int m = nw / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int box_cells = a.g.box[0];
+    const int slot = (box_cells + 1) / 2 * 2;
+    const int nbmax = a.spread_batch;
+    const int sub = a.spread_sub;
+    const SpreadSmem Ls = spread_smem_layout<T>(1, A, box_cells, nbmax, sub);
+    unsigned char* boxc = smem + Ls.box;
+    unsigned long long* boxz = reinterpret_cast<unsigned long long*>(boxc);
+    int* s_lb = reinterpret_cast<int*>(smem + Ls.lb);
+    T* s_w = reinterpret_cast<T*>(smem + Ls.w);
+    CT* s_g = reinterpret_cast<CT*>(smem + Ls.g);
+    int* s_run = reinterpret_cast<int*>(smem + Ls.run);
+    double* s_red = reinterpret_cast<double*>(smem + Ls.red);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    const int wk = weight_kind(a.w);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int G = 32 / nw;        // row groups per warp
+    const int c = lane % nw;      // owned tap
+    const int rg = lane / nw;     // row group
+    const bool active = rg < G;
+    for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+        const WorkItem wi = a.work[item];
+        int org[3] = {0, 0, 0};
+        tile_origin<1>(a.g, wi.tile, periodic, org);
+        for (int b0 = 0; b0 < a.batch; b0 += nbmax) {
+            const int nb = min(nbmax, a.batch - b0);
+            item_abs_sum<T>(a, wi, b0, nb, s_red);
+            for (int idx = tid; idx < nb * slot * 2; idx += blockDim.x) boxz[idx] = 0ull;
+            __syncthreads();
+            if (tid == 0) item_quantum<T>(a, nwarps, s_red);
+            __syncthreads();
+            const ItemQuantum<T> iq(s_red);
+            if (iq.any) {
+                for (int s0 = 0; s0 < wi.count; s0 += sub) {
+                    const int ns = min(sub, wi.count - s0);
+                    if (tid < ns) {
+                        const long long i = static_cast<long long>(wi.start) + s0 + tid;
+                        T tau[3];
+                        int lb[3] = {0, 0, 0};
+                        node_setup<T, 1>(a.xs, i, a.g, org, tau, lb, m);
+                        s_lb[tid] = lb[0];
+                        tap_weights_to<T, W>(s_w + static_cast<size_t>(tid) * A, wk, tau[0], a.w);
+                        const long long src = a.perm[i];
+                        for (int bb = 0; bb < nb; ++bb) {
+                            const CT gv = a.fin[static_cast<long long>(b0 + bb) * a.N + src];
+                            s_g[bb * sub + tid] = cmake<T>(gv.x * iq.inv_q, gv.y * iq.inv_q);
+                        }
+                    }
+                    __syncthreads();
+                    // runs of equal first taps (same cell), indexed in order
+                    const int flag = (tid < ns) && (tid == 0 || s_lb[tid] != s_lb[tid - 1]);
+                    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+                    const int before = __popc(bal & ((1u << lane) - 1u));
+                    if (lane == 0) s_red[warp] = __popc(bal);
+                    __syncthreads();
+                    int wbase = 0, nruns = 0;
+                    for (int w = 0; w < warp; ++w) wbase += static_cast<int>(s_red[w]);
+                    for (int w = 0; w < nwarps; ++w) nruns += static_cast<int>(s_red[w]);
+                    if (flag) s_run[wbase + before] = tid;
+                    if (tid == 0) s_run[nruns] = ns;
+                    __syncthreads();
+                    if (active) {
+                        for (int r = warp; r < nruns; r += nwarps) {
+                            const int jlo = s_run[r], jhi = s_run[r + 1];
+                            const int lb0 = s_lb[jlo];
+                            for (int bb = 0; bb < nb; ++bb) {
+                                const CT* gg = s_g + bb * sub;
+                                T ar = T(0), ai = T(0);
+                                for (int j = jlo + rg; j < jhi; j += G) {
+                                    const T wv = s_w[static_cast<size_t>(j) * A + c];
+                                    ar += gg[j].x * wv;
+                                    ai += gg[j].y * wv;
+                                }
+                                FixedCell<T>::add(boxc + static_cast<size_t>(bb) * slot * 16, lb0 + c, slot, ar, ai);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < nb * box_cells; idx += blockDim.x) {
+                const int bb = idx / box_cells;
+                const int cell = idx - bb * box_cells;
+                const unsigned char* grp = boxc + static_cast<size_t>(bb) * slot * 16;
+                CT v;
+                v.x = FixedCell<T>::value(grp, cell, slot, 0, iq.q_lo, iq.q_hi);
+                v.y = FixedCell<T>::value(grp, cell, slot, 1, iq.q_lo, iq.q_hi);
+                a.part[(static_cast<long long>(item) * a.batch + b0 + bb) * box_cells + cell] = v;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Ordered flush: grid[b][l] = sum over the boxes covering l, in a fixed order.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) gather_kernel(const TapArgs<T> a) {
@@ -1706,10 +1566,11 @@ template <typename T, int D, int W>
 nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem) {
     void* fn = nullptr;
     if (kind == TAP_INTERP) fn = reinterpret_cast<void*>(interp_kernel<T, D, W>);
-    if (kind == TAP_SPREAD)
-        fn = (D == 2)   ? reinterpret_cast<void*>(spread2_kernel<T, W>)
-             : (D == 3) ? reinterpret_cast<void*>(spread3_kernel<T, W>)
-                        : reinterpret_cast<void*>(spread_kernel<T, D, W>);
+    if (kind == TAP_SPREAD) {
+        if constexpr (D == 1) fn = reinterpret_cast<void*>(spread1_kernel<T, W>);
+        else if constexpr (D == 2) fn = reinterpret_cast<void*>(spread2_kernel<T, W>);
+        else fn = reinterpret_cast<void*>(spread3_kernel<T, W>);
+    }
     const int threads = (kind == TAP_SPREAD && D == 3) ? 32 * args.spread_warps : kTapThreads;
     if (kind == TAP_GRAD) fn = reinterpret_cast<void*>(node_grad_kernel<T, D, W>);
     if (kind == TAP_FACTORS) {
@@ -1739,12 +1600,11 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     timing_begin(p, kind == TAP_INTERP ? NFFTBL_K_INTERP : kind == TAP_SPREAD ? NFFTBL_K_SPREAD : NFFTBL_K_GRAD);
     if (kind == TAP_INTERP)
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
-    else if (kind == TAP_SPREAD && D == 2)
-        spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
-    else if (kind == TAP_SPREAD && D == 3)
-        spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
-    else if (kind == TAP_SPREAD)
-        spread_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(args);
+    else if (kind == TAP_SPREAD) {
+        if constexpr (D == 1) spread1_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
+        else if constexpr (D == 2) spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
+        else spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
+    }
     else
         node_grad_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
     timing_end(p);
