@@ -94,9 +94,10 @@ __host__ __device__ __forceinline__ SpreadSmem spread_smem_layout(int d, int A, 
 }
 
 // Row length (elements) of spread2_kernel's per-warp node table: 2A window
-// values, the input value (2 elements), the packed first taps (an int in the
-// next element) and one element of padding; with A even every row starts
-// 16-byte aligned and consecutive rows fall on different bank groups.
+// values, the input value (2 elements), the segment key and the first
+// column within the segment (an int in each of the last two elements); with
+// A even every row starts 16-byte aligned and consecutive rows fall on
+// different bank groups.
 template <typename T>
 __host__ __device__ constexpr int spread2_row(int A) {
     return 2 * A + 4;

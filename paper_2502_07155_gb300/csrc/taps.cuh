@@ -1008,7 +1008,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
     using CT = C2<T>;
     using U = unsigned long long;
     constexpr int A = TapN<W>::A;
-    constexpr int RS = spread2_row<T>(A);   // node-table row: w0[A] | w1[A] | g.x g.y lb pad
+    constexpr int RS = spread2_row<T>(A);   // node-table row: w0[A] | w1[A] | g.x g.y | key t0
     static_assert(A % 2 == 0, "node-table rows must stay 16-byte aligned");
     const int nw = W ? W : 2 * a.w.m;
     const int m = nw / 2;
@@ -1094,27 +1094,31 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             }
                             row[2 * A] = cg.x * inv_q;
                             row[2 * A + 1] = cg.y * inv_q;
-                            reinterpret_cast<int*>(row + 2 * A + 2)[0] = lb[0] | (lb[1] << 16);
+                            // segment key (box row, column segment) and the node's first
+                            // column within its segment: lane l's column is base + l,
+                            // so its tap index is l - t0
+                            const int segc = lb[1] / S;
+                            int* ri = reinterpret_cast<int*>(row + 2 * A + 2);
+                            ri[0] = lb[0] | (segc << 16);
+                            ri[1] = lb[1] - segc * S;
                         }
                         __syncwarp();
                         load_g(c0 + 32);
                         // ---- phase B: walk the chunk (two nodes at a time while both
                         // stay in the current segment)
-                        auto seg_key = [&](int lbk) { return (lbk & 0xFFFF) | (((lbk >> 16) / S) << 16); };
                         auto one = [&](const T* row) {
-                            const int lbk = reinterpret_cast<const int*>(row + 2 * A + 2)[0];
-                            const int lb0 = lbk & 0xFFFF, lb1 = lbk >> 16;
-                            const int key = seg_key(lbk);
+                            const int* ri = reinterpret_cast<const int*>(row + 2 * A + 2);
+                            const int key = ri[0];
                             if (key != seg) {
                                 if (seg >= 0) flush();
                                 seg = key;
-                                seg_lb0 = lb0;
-                                col = (lb1 / S) * S + lane;
+                                seg_lb0 = key & 0xFFFF;
+                                col = (key >> 16) * S + lane;
 #pragma unroll
                                 for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
                             }
-                            const int t = col - lb1;
-                            const bool in = (t >= 0) && (t < nw);
+                            const int t = lane - ri[1];
+                            const bool in = static_cast<unsigned>(t) < static_cast<unsigned>(nw);
                             const T wf = in ? row[A + (in ? t : 0)] : T(0);
                             const T gr = row[2 * A] * wf, gi = row[2 * A + 1] * wf;
                             T w0r[A];
@@ -1132,11 +1136,12 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                         for (; W != 0 && k + 1 < nc; k += 2) {   // (runtime-m kernels walk singly)
                             const T* ra = s_tab + k * RS;
                             const T* rb = ra + RS;
-                            const int la = reinterpret_cast<const int*>(ra + 2 * A + 2)[0];
-                            const int lbb = reinterpret_cast<const int*>(rb + 2 * A + 2)[0];
-                            if (seg_key(la) == seg && seg_key(lbb) == seg) {
-                                const int ta = col - (la >> 16), tb = col - (lbb >> 16);
-                                const bool ina = (ta >= 0) && (ta < nw), inb = (tb >= 0) && (tb < nw);
+                            const int* ria = reinterpret_cast<const int*>(ra + 2 * A + 2);
+                            const int* rib = reinterpret_cast<const int*>(rb + 2 * A + 2);
+                            if (ria[0] == seg && rib[0] == seg) {
+                                const int ta = lane - ria[1], tb = lane - rib[1];
+                                const bool ina = static_cast<unsigned>(ta) < static_cast<unsigned>(nw);
+                                const bool inb = static_cast<unsigned>(tb) < static_cast<unsigned>(nw);
                                 const T wfa = ina ? ra[A + (ina ? ta : 0)] : T(0);
                                 const T wfb = inb ? rb[A + (inb ? tb : 0)] : T(0);
                                 const T gra = ra[2 * A] * wfa, gia = ra[2 * A + 1] * wfa;
