@@ -1106,9 +1106,12 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                         load_g(c0 + 32);
                         // ---- phase B: walk the chunk (two nodes at a time while both
                         // stay in the current segment)
+                        // per-node meta data: the input value and (key, t0), one vector each
+                        auto meta_g = [&](const T* row) { return *reinterpret_cast<const CT*>(row + 2 * A); };
+                        auto meta_k = [&](const T* row) { return *reinterpret_cast<const int2*>(row + 2 * A + 2); };
                         auto one = [&](const T* row) {
-                            const int* ri = reinterpret_cast<const int*>(row + 2 * A + 2);
-                            const int key = ri[0];
+                            const int2 kt = meta_k(row);
+                            const int key = kt.x;
                             if (key != seg) {
                                 if (seg >= 0) flush();
                                 seg = key;
@@ -1117,10 +1120,11 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
 #pragma unroll
                                 for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
                             }
-                            const int t = lane - ri[1];
+                            const int t = lane - kt.y;
                             const bool in = static_cast<unsigned>(t) < static_cast<unsigned>(nw);
                             const T wf = in ? row[A + (in ? t : 0)] : T(0);
-                            const T gr = row[2 * A] * wf, gi = row[2 * A + 1] * wf;
+                            const CT g = meta_g(row);
+                            const T gr = g.x * wf, gi = g.y * wf;
                             T w0r[A];
                             load_row<T, A>(row, w0r);
 #pragma unroll
@@ -1136,16 +1140,16 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                         for (; W != 0 && k + 1 < nc; k += 2) {   // (runtime-m kernels walk singly)
                             const T* ra = s_tab + k * RS;
                             const T* rb = ra + RS;
-                            const int* ria = reinterpret_cast<const int*>(ra + 2 * A + 2);
-                            const int* rib = reinterpret_cast<const int*>(rb + 2 * A + 2);
-                            if (ria[0] == seg && rib[0] == seg) {
-                                const int ta = lane - ria[1], tb = lane - rib[1];
+                            const int2 kta = meta_k(ra), ktb = meta_k(rb);
+                            if (kta.x == seg && ktb.x == seg) {
+                                const int ta = lane - kta.y, tb = lane - ktb.y;
                                 const bool ina = static_cast<unsigned>(ta) < static_cast<unsigned>(nw);
                                 const bool inb = static_cast<unsigned>(tb) < static_cast<unsigned>(nw);
                                 const T wfa = ina ? ra[A + (ina ? ta : 0)] : T(0);
                                 const T wfb = inb ? rb[A + (inb ? tb : 0)] : T(0);
-                                const T gra = ra[2 * A] * wfa, gia = ra[2 * A + 1] * wfa;
-                                const T grb = rb[2 * A] * wfb, gib = rb[2 * A + 1] * wfb;
+                                const CT ga = meta_g(ra), gb = meta_g(rb);
+                                const T gra = ga.x * wfa, gia = ga.y * wfa;
+                                const T grb = gb.x * wfb, gib = gb.y * wfb;
                                 T wa[A], wb[A];
                                 load_row<T, A>(ra, wa);
                                 load_row<T, A>(rb, wb);
