@@ -71,10 +71,13 @@ SM_MAX_MHZ = 2070.0
 # SFU slots per tap weight of the sinh window: rsqrt + rcp + 2 ex2 (1/2 each)
 SFU_SLOTS_PER_WEIGHT = 3.0
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of this workload: filled from the committed profile summary of the
-# same kernel version, None when not yet captured.
-NCU_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of the short-sum kernels from one ncu
+# capture of the same workload and kernel version (the launch-list profile
+# summary of each workload); absent when not captured for the current code.
+NCU_TRAFFIC_BYTES = {
+    ("d2_M256_m8_N2^20", "spread"): 21115904,
+    ("d2_M256_m8_N2^20", "interp"): 14765568,
+}
 
 
 def short_sum_roofline(d, m, N, B, M, seconds):
