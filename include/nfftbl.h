@@ -112,9 +112,11 @@ void nfftbl_default_opts(nfftbl_opts* opts);
  * diagonal D_psihat = diag(1/(|I_L| psi_hat(k))) of Eq. 4.9 (D of Eq. 2.2) in
  * tensor-product form.  Runs on the legacy default stream and synchronises.
  * Errors: EINVAL (d, M odd or < 2, sigma < 1, m < 1, 2m >= L_t, batch < 1,
- * bad table or tile, beta <= 0 after defaults), EUNSUPPORTED (L_t not a
- * power of two in [16, 4096], m outside 2..12, prod L_t >= 2^31, a box of
- * tile plus halo beyond shared memory), ENOMEM, ECUDA.  The message of a
+ * bad table or tile, beta <= 0 after defaults), EUNSUPPORTED (L_t not of
+ * the form 2^a 3^b 5^c in [16, 4096] -- the FFT's radices --, m outside
+ * 2..12, prod L_t > 2^31, a box of tile plus halo beyond shared memory),
+ * ENOMEM, ECUDA.  Tiles are the largest power of two (up to 64 / 32^2 / 8^3
+ * for d = 1 / 2 / 3) dividing L_t.  The message of a
  * failed call is available from nfftbl_plan_error().
  */
 nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m,

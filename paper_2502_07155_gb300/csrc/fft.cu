@@ -12,7 +12,7 @@
 // k in I_{M_t} multiplied by (-1)^k d_t(k)  (F^H and D_psihat of Eq. 4.11).
 //
 // Each CTA transforms W lines of one pass in shared memory with a
-// mixed-radix (4, then 2) Stockham autosort FFT; twiddles come from an FP64
+// mixed-radix (4, 2, 3, 5) Stockham autosort FFT; twiddles come from an FP64
 // table rounded to the plan's precision.
 #include <algorithm>
 
@@ -130,53 +130,75 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
     }
     __syncthreads();
 
-    // ---- Stockham stages: radix 4 while possible, then radix 2
+    // ---- Stockham stages: radix 4 while possible, then 2, 3 and 5
+    // (L = 2^a 3^b 5^c).  Stage with radix r and span s (the product of the
+    // earlier radices): butterfly i (k = i mod s) reads i + j L/r, multiplies
+    // input j by w^(j k L/(r s)) and writes (i - k) r + k + j s; every
+    // twiddle exponent stays below L.
     CT* src = bufA;
     CT* dst = bufB;
-    int span = 1;
+    int span = 1, rem = L;
     while (span < L) {
-        const int r = (span * 4 <= L) ? 4 : 2;
+        const int r = (rem % 4 == 0) ? 4 : (rem % 2 == 0) ? 2 : (rem % 3 == 0) ? 3 : 5;
         const int nb = L / r;
         const int tstep = L / (r * span);
         for (int b = tid; b < W * nb; b += blockDim.x) {
             const int w = b / nb;
             const int i = b - w * nb;
-            const int k = i & (span - 1);
+            const int k = i % span;
             const CT* s = src + w * pitch;
             CT* dd = dst + w * pitch;
             const int obase = (i - k) * r + k;
+            CT c[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (j < r) c[j] = s[i + j * nb];
+            if (span > 1) {
+                const int e = k * tstep;
+#pragma unroll
+                for (int j = 1; j < 5; ++j)
+                    if (j < r) c[j] = ADJ ? cmulc<T>(c[j], twd[j * e]) : cmul<T>(c[j], twd[j * e]);
+            }
+            // multiplication by +i (forward: inverse-DFT sign) or -i (adjoint)
+            auto rot = [](CT v) { return ADJ ? cmake<T>(v.y, -v.x) : cmake<T>(-v.y, v.x); };
             if (r == 4) {
-                CT c0 = s[i], c1 = s[i + nb], c2 = s[i + 2 * nb], c3 = s[i + 3 * nb];
-                if (span > 1) {
-                    const int e = k * tstep;
-                    if (!ADJ) {
-                        c1 = cmul<T>(c1, twd[e & (L - 1)]);
-                        c2 = cmul<T>(c2, twd[(2 * e) & (L - 1)]);
-                        c3 = cmul<T>(c3, twd[(3 * e) & (L - 1)]);
-                    } else {
-                        c1 = cmulc<T>(c1, twd[e & (L - 1)]);
-                        c2 = cmulc<T>(c2, twd[(2 * e) & (L - 1)]);
-                        c3 = cmulc<T>(c3, twd[(3 * e) & (L - 1)]);
-                    }
-                }
-                const CT a0 = cmake<T>(c0.x + c2.x, c0.y + c2.y);
-                const CT a1 = cmake<T>(c0.x - c2.x, c0.y - c2.y);
-                const CT a2 = cmake<T>(c1.x + c3.x, c1.y + c3.y);
-                const CT dm = cmake<T>(c1.x - c3.x, c1.y - c3.y);
-                // a3 = (c1 - c3) * (s i), s = +1 forward (inverse DFT), -1 adjoint
-                const CT a3 = ADJ ? cmake<T>(dm.y, -dm.x) : cmake<T>(-dm.y, dm.x);
+                const CT a0 = cmake<T>(c[0].x + c[2].x, c[0].y + c[2].y);
+                const CT a1 = cmake<T>(c[0].x - c[2].x, c[0].y - c[2].y);
+                const CT a2 = cmake<T>(c[1].x + c[3].x, c[1].y + c[3].y);
+                const CT a3 = rot(cmake<T>(c[1].x - c[3].x, c[1].y - c[3].y));
                 dd[obase] = cmake<T>(a0.x + a2.x, a0.y + a2.y);
                 dd[obase + span] = cmake<T>(a1.x + a3.x, a1.y + a3.y);
                 dd[obase + 2 * span] = cmake<T>(a0.x - a2.x, a0.y - a2.y);
                 dd[obase + 3 * span] = cmake<T>(a1.x - a3.x, a1.y - a3.y);
+            } else if (r == 2) {
+                dd[obase] = cmake<T>(c[0].x + c[1].x, c[0].y + c[1].y);
+                dd[obase + span] = cmake<T>(c[0].x - c[1].x, c[0].y - c[1].y);
+            } else if (r == 3) {
+                // y1,2 = c0 - (c1 + c2)/2 +- (rot) (sqrt(3)/2)(c1 - c2)
+                const T h = static_cast<T>(0.86602540378443864676);
+                const CT t1 = cmake<T>(c[1].x + c[2].x, c[1].y + c[2].y);
+                const CT t2 = cmake<T>(c[0].x - T(0.5) * t1.x, c[0].y - T(0.5) * t1.y);
+                const CT t3 = rot(cmake<T>(h * (c[1].x - c[2].x), h * (c[1].y - c[2].y)));
+                dd[obase] = cmake<T>(c[0].x + t1.x, c[0].y + t1.y);
+                dd[obase + span] = cmake<T>(t2.x + t3.x, t2.y + t3.y);
+                dd[obase + 2 * span] = cmake<T>(t2.x - t3.x, t2.y - t3.y);
             } else {
-                CT c0 = s[i], c1 = s[i + nb];
-                if (span > 1) {
-                    const int e = (k * tstep) & (L - 1);
-                    c1 = ADJ ? cmulc<T>(c1, twd[e]) : cmul<T>(c1, twd[e]);
-                }
-                dd[obase] = cmake<T>(c0.x + c1.x, c0.y + c1.y);
-                dd[obase + span] = cmake<T>(c0.x - c1.x, c0.y - c1.y);
+                // radix 5 with cos/sin of 2 pi/5 and 4 pi/5
+                const T c1 = static_cast<T>(0.30901699437494742410), c2 = static_cast<T>(-0.80901699437494742410);
+                const T s1 = static_cast<T>(0.95105651629515357212), s2 = static_cast<T>(0.58778525229247312917);
+                const CT t1 = cmake<T>(c[1].x + c[4].x, c[1].y + c[4].y);
+                const CT t2 = cmake<T>(c[2].x + c[3].x, c[2].y + c[3].y);
+                const CT t3 = cmake<T>(c[1].x - c[4].x, c[1].y - c[4].y);
+                const CT t4 = cmake<T>(c[2].x - c[3].x, c[2].y - c[3].y);
+                const CT a1 = cmake<T>(c[0].x + c1 * t1.x + c2 * t2.x, c[0].y + c1 * t1.y + c2 * t2.y);
+                const CT a2 = cmake<T>(c[0].x + c2 * t1.x + c1 * t2.x, c[0].y + c2 * t1.y + c1 * t2.y);
+                const CT b1 = rot(cmake<T>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+                const CT b2 = rot(cmake<T>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+                dd[obase] = cmake<T>(c[0].x + t1.x + t2.x, c[0].y + t1.y + t2.y);
+                dd[obase + span] = cmake<T>(a1.x + b1.x, a1.y + b1.y);
+                dd[obase + 2 * span] = cmake<T>(a2.x + b2.x, a2.y + b2.y);
+                dd[obase + 3 * span] = cmake<T>(a2.x - b2.x, a2.y - b2.y);
+                dd[obase + 4 * span] = cmake<T>(a1.x - b1.x, a1.y - b1.y);
             }
         }
         __syncthreads();
@@ -184,6 +206,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
         src = dst;
         dst = tmp;
         span *= r;
+        rem /= r;
     }
 
     // ---- store

@@ -15,6 +15,14 @@ namespace {
 thread_local std::string g_plan_error;
 
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// v = 2^a 3^b 5^c (the FFT's radices)
+bool is_235(long long v) {
+    if (v <= 0) return false;
+    for (int r : {2, 3, 5})
+        while (v % r == 0) v /= r;
+    return v == 1;
+}
 int ilog2(long long v) {
     int r = 0;
     while ((1LL << r) < v) ++r;
@@ -383,8 +391,8 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
         if (2 * m >= L[t]) return plan_fail(nullptr, NFFTBL_EINVAL, "2m must be < L_t");
     }
     for (int t = 0; t < d; ++t)
-        if (!is_pow2(L[t]) || L[t] < 16 || L[t] > 4096)
-            return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "L_t must be a power of two in [16, 4096]");
+        if (!is_235(L[t]) || L[t] < 16 || L[t] > 4096)
+            return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "L_t must be of the form 2^a 3^b 5^c in [16, 4096]");
     if (m < 2 || m > 12) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "m must be in 2..12");
     double beta = o.beta;
     if (!(beta > 0.0)) {
@@ -393,16 +401,24 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
         if (window == NFFTBL_WIN_TABLE) beta = 1.0;   // unused by a tabulated window
     }
     if (!(beta > 0.0)) return plan_fail(nullptr, NFFTBL_EINVAL, "beta must be > 0 (sigma = 1 needs an explicit beta)");
+    // cell keys are < prod L_t (tile-major, then in-tile row-major)
+    long long cells_total = 1;
+    for (int t = 0; t < d; ++t) cells_total *= L[t];
     int key_bits = 0;
-    for (int t = 0; t < d; ++t) key_bits += ilog2(L[t]);
-    if (key_bits > 31) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "prod L_t must be < 2^31");
+    while ((1LL << key_bits) < cells_total) ++key_bits;
+    if (key_bits > 31) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "prod L_t must be <= 2^31");
 
     // tile shape
     const int def_tile = (d == 1) ? 64 : (d == 2) ? 32 : 8;
     int T[3] = {1, 1, 1};
     const bool user_tile = o.tile[0] > 0;
     for (int t = 0; t < d; ++t) {
-        T[t] = user_tile ? o.tile[t] : std::min(def_tile, L[t]);
+        if (user_tile) {
+            T[t] = o.tile[t];
+        } else {   // the largest power of two <= the default that divides L_t
+            T[t] = 1;
+            while (2 * T[t] <= def_tile && L[t] % (2 * T[t]) == 0) T[t] *= 2;
+        }
         if (!is_pow2(T[t]) || T[t] < 2 || L[t] % T[t] != 0)
             return plan_fail(nullptr, NFFTBL_EINVAL, "tile extents must be powers of two >= 2 dividing L_t");
     }

@@ -164,6 +164,50 @@ def test_stored_factors_match_evaluated(d, prec, method, window):
     assert rel_l2(outs[True][1], outs[False][1]) < agree
 
 
+GENERAL_L = [
+    (1, 20, 5, "f64", "shannon"),            # L = 40 = 2^3 5
+    (1, 20, 5, "f32", "classic"),
+    (1, 100, 5, "f64", "shannon"),           # L = 200 = 2^3 5^2
+    (2, (20, 24), 4, "f64", "shannon"),      # L = (40, 48 = 2^4 3)
+    (2, (20, 24), 4, "f32", "classic"),
+    (2, (30, 36), 3, "f32", "shannon"),      # L = (60 = 2^2 3 5, 72 = 2^3 3^2)
+    (3, (12, 10, 18), 3, "f64", "shannon"),  # L = (24, 20, 36)
+    (3, 12, 3, "f32", "classic"),
+]
+
+
+@pytest.mark.parametrize("d,M,m,prec,method", GENERAL_L)
+def test_general_L_parity(d, M, m, prec, method):
+    """sigma = 2 with M_t not a power of two: L_t = 2^a 3^b 5^c (mixed-radix
+    FFT passes, power-of-two tiles dividing L_t).  Binning bit-exact; grid
+    (Eq. 4.7), forward and adjoint against the oracle."""
+    batch = 2
+    plan = nb.Plan(d, M, 2.0, m, precision=prec, method=method, batch=batch)
+    assert any(L & (L - 1) for L in plan.L)
+    x = W.nodes_uniform(2000, d, dtype=RDT[prec], seed=4)
+    plan.set_nodes(to_dev(x))
+    keys, perm, off = plan.binning()
+    rk, rp, roff, ok = O.bin_nodes(x, plan.L, plan.info()["tile"][:d])
+    assert ok
+    np.testing.assert_array_equal(perm.astype(np.int64), rp)
+    np.testing.assert_array_equal(off.astype(np.int64), roff)
+    op = oracle_plan(plan)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+    f = to_host(plan.forward(to_dev(fh)))
+    assert rel_l2(plan.grid(), O.grid_samples(op, fh)) < TOL[prec]
+    assert rel_l2(f, O.forward(op, fh, x)) < TOL[prec]
+    g = W.adjoint_input(x.shape[0], batch=batch, dtype=CDT[prec])
+    h = to_host(plan.adjoint(to_dev(g)))
+    plan.sync()
+    assert rel_l2(h, O.adjoint(op, g, x)) < TOL[prec]
+
+
+def test_general_L_rejects_other_primes():
+    with pytest.raises(nb.NfftblError) as e:
+        nb.Plan(1, 14, 2.0, 3)        # L = 28 = 2^2 7
+    assert e.value.name == "EUNSUPPORTED"
+
+
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_adjoint_identity_gpu(d):
     """<A fhat, g> = <fhat, A^H g> with both sides from the GPU (FP64)."""
