@@ -127,6 +127,39 @@ def aggregate_over_ranks(t_step_ms, units_per_rank, world, device=None):
     return t_step_ms, world * units_per_rank / (t_step_ms * 1e-3)
 
 
+def run_paper(args):
+    """The paper's experiments on the GPU (Section 5): Example 5.1 for both
+    algorithms in FP64 and FP32, and Fig. 5.1's e(v) at P = 10^5 points for
+    961 frequencies (one batched interpolation per curve).  Prints one JSON
+    line with the errors and the times."""
+    import torch
+    from paper_2502_07155_gb300 import build
+    build.build()
+    from paper_2502_07155_gb300.experiments import example51_errors, fig51_errors
+    torch.cuda.set_device(0)
+    Ms = [20, 40, 80, 100, 200, 400, 600, 800, 1000]
+    ex = {str(M): {f"{meth}_{prec}": example51_errors(M, 5, prec, meth) for meth in ("shannon", "classic")
+                   for prec in ("f64", "f32")} for M in Ms}
+    beta_sh = float(np.pi * 5 * 0.5)
+    curves = {}
+    for name, kw in [("shannon_full", dict(interval="full")), ("shannon_trunc", dict(interval="trunc")),
+                     ("classic_full", dict(interval="full", method="classic")),
+                     ("classic_trunc", dict(interval="trunc", method="classic")),
+                     ("classic_trunc_beta_shannon", dict(interval="trunc", method="classic", beta=beta_sh))]:
+        fig51_errors(P=1000, **kw)   # warm-up (builds the plan's kernels)
+        v, e, sec = fig51_errors(P=100_000, **kw)
+        inner = np.abs(v) <= 9
+        nonint = inner & (np.abs(v - np.round(v)) > 1e-9)
+        integ = inner & ~nonint
+        curves[name] = {"median_nonint_inner": float(np.median(e[nonint])), "max_nonint_inner": float(e[nonint].max()),
+                        "max_int_inner": float(e[integ].max()), "interp_seconds": sec,
+                        "node_evaluations_per_s": v.size * 100_000 / sec}
+    print(json.dumps({"metric": "paper experiments on GPU (Example 5.1 max error; Fig. 5.1 e(v))",
+                      "example_5_1": ex, "fig_5_1": {"M": 20, "m": 5, "S": 32, "P": 100_000, "frequencies": 961,
+                                                      "curves": curves}}))
+    return 0
+
+
 def run_unit_rates():
     """Build and run the unit-rate microbenchmark (FP32 FMA, ex2, rsqrt, rcp
     lane operations per SM per clock); prints one JSON line per unit."""
@@ -633,6 +666,7 @@ def main():
     ap.add_argument("--learned-m", type=int, nargs="+", default=[2, 3, 4], dest="learned_m")
     ap.add_argument("--learned-steps", type=int, default=1500, dest="learned_steps")
     ap.add_argument("--learned-lr", type=float, default=3e-3, dest="learned_lr")
+    ap.add_argument("--paper", action="store_true", help="run the paper's experiments (Example 5.1, Fig. 5.1)")
     ap.add_argument("--unit-rates", action="store_true", dest="unit_rates",
                     help="measure FP32 FMA and SFU lane rates per SM (roofline peaks)")
     ap.add_argument("--no-graph", action="store_true", dest="no_graph",
@@ -644,6 +678,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.unit_rates:
         return run_unit_rates()
+    if args.paper:
+        return run_paper(args)
     if args.impl == "reference":
         return run_reference(args, args.config)
     if args.learned:

@@ -228,6 +228,15 @@ nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t plan, void** grid_dev);
  * cleared first).  For experiments that supply equispaced samples directly,
  * such as the exponential approximations of Eqs. 5.1-5.2.
  */
+/* The window transform at arbitrary real frequencies v (Eq. 4.2 for the
+ * Shannon method: psi_hat(v) = int sinc(L pi x) phi(x) e^{-2 pi i v x} dx;
+ * phi_hat(v) for CLASSIC), dimension t, in FP64 by the plan's own device
+ * quadrature (the rule of step 0a).  v_dev, out_dev: device arrays of n
+ * doubles.  Used for approximations at non-integer frequencies (Section 5,
+ * Fig. 5.1: the classical approximation divides by L phi_hat(v)).
+ * Asynchronous on the plan's stream.  Errors: EINVAL (t, n, NULL). */
+nfftbl_status nfftbl_window_transform(nfftbl_plan_t plan, int t, const double* v_dev, int n, double* out_dev);
+
 nfftbl_status nfftbl_interp_grid(nfftbl_plan_t plan, void* f_dev);
 nfftbl_status nfftbl_spread_grid(nfftbl_plan_t plan, const void* f_dev);
 

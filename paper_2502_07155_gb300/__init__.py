@@ -37,7 +37,7 @@ EXPORTED = [
     "nfftbl_grid_ptr", "nfftbl_interp_grid", "nfftbl_spread_grid", "nfftbl_kernel_launches",
     "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
     "nfftbl_set_window_table", "nfftbl_window_loss_grad", "nfftbl_mlp_table", "nfftbl_mlp_backward",
-    "nfftbl_mlp_param_count", "nfftbl_mlp_scratch_floats", "nfftbl_adam_step",
+    "nfftbl_mlp_param_count", "nfftbl_mlp_scratch_floats", "nfftbl_adam_step", "nfftbl_window_transform",
 ]
 KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin", "flush")
 
@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_grid_ptr.restype = st
     L.nfftbl_interp_grid.argtypes = [P, P]
     L.nfftbl_interp_grid.restype = st
+    L.nfftbl_window_transform.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
+    L.nfftbl_window_transform.restype = st
     L.nfftbl_spread_grid.argtypes = [P, P]
     L.nfftbl_spread_grid.restype = st
     L.nfftbl_kernel_launches.argtypes = [P]
@@ -288,6 +290,17 @@ class Plan:
         po = self._dev(out, self._cdtype, (self.batch, max(self.n_nodes, 0)), "out")
         self._stream()
         self._check(self._lib.nfftbl_interp_grid(self._h, po))
+        return out
+
+    def window_transform(self, v, t: int = 0):
+        """psi_hat(v) (phi_hat for the classical method) of dimension t at the
+        real frequencies v (a float64 CUDA tensor), by the plan's quadrature."""
+        torch = _torch()
+        v = v.to(device="cuda", dtype=torch.float64).contiguous()
+        out = torch.empty_like(v)
+        self._stream()
+        self._check(self._lib.nfftbl_window_transform(self._h, int(t), ctypes.c_void_p(v.data_ptr()), v.numel(),
+                                                      ctypes.c_void_p(out.data_ptr())))
         return out
 
     def spread_grid(self, f):

@@ -615,6 +615,21 @@ nfftbl_status nfftbl_node_grad(nfftbl_plan_t p, const void* fhat_dev, const void
     return taps(p, TAP_GRAD, gradf_dev, nullptr, gradx_dev);
 }
 
+nfftbl_status nfftbl_window_transform(nfftbl_plan_t p, int t, const double* v_dev, int n, double* out_dev) {
+    if (!p) return NFFTBL_EINVAL;
+    if (t < 0 || t >= p->d) return fail(p, NFFTBL_EINVAL, "dimension t out of range");
+    if (n < 0 || (n > 0 && (!v_dev || !out_dev))) return fail(p, NFFTBL_EINVAL, "bad frequency list");
+    const double* tab64 = nullptr;
+    if (p->window == NFFTBL_WIN_TABLE)
+        tab64 = static_cast<const double*>((p->precision == NFFTBL_F64) ? p->table_dev.p : p->table_dev64.p);
+    nfftbl_status st = check_cuda(p, launch_window_transform(p->method == NFFTBL_SHANNON, p->window, p->L[t], p->m,
+                                                             p->beta, tab64, static_cast<int>(p->table_host.size()) - 1,
+                                                             v_dev, n, out_dev, p->stream),
+                                  "window transform");
+    if (st == NFFTBL_OK && n > 0) p->launches++;
+    return st;
+}
+
 nfftbl_status nfftbl_interp_grid(nfftbl_plan_t p, void* f_dev) {
     nfftbl_status st = ready(p);
     if (st != NFFTBL_OK) return st;

@@ -259,6 +259,8 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
                                   cudaStream_t s);
 cudaError_t launch_cast_factors(const double* fac64, int M, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s);
+cudaError_t launch_window_transform(int with_sinc, int window, int L, int m, double beta, const double* table,
+                                    int table_n, const double* v, int n, double* out, cudaStream_t s);
 cudaError_t launch_table_cast(const double* in, int n, float* out, float4* coef, cudaStream_t s);
 cudaError_t launch_window_table_grad(int L, int M, int m, int table_n, const double* dEdpsi, double* grad,
                                      cudaStream_t s);

@@ -70,11 +70,13 @@ __device__ double catmull_rom_d(const double* v, int n, double u) {
                   (3.0 * p1 - p0 - 3.0 * p2 + p3) * t * t * t);
 }
 
+// One block per frequency: k = kidx - M/2 (vlist == NULL; writes the factor
+// 1/(L psi_hat(k))) or k = vlist[kidx] (writes psi_hat(k) itself).
 __global__ void window_factor_kernel(int with_sinc, int window, int L, int M, int m, double beta,
                                      const double* __restrict__ table, int table_n, int panels,
-                                     double* __restrict__ fac_out) {
+                                     const double* __restrict__ vlist, double* __restrict__ fac_out) {
     const int kidx = blockIdx.x;
-    const double k = static_cast<double>(kidx - M / 2);
+    const double k = vlist ? vlist[kidx] : static_cast<double>(kidx - M / 2);
     const double h = 0.5 * M_PI / panels;           // panel width in theta
     const double ml = static_cast<double>(m) / L;    // support half-width m/L
     double norm = 1.0;
@@ -113,7 +115,7 @@ __global__ void window_factor_kernel(int with_sinc, int window, int L, int M, in
     if (threadIdx.x == 0) {
         double tot = 0.0;
         for (int w = 0; w < (blockDim.x + 31) / 32; ++w) tot += part[w];
-        fac_out[kidx] = 1.0 / (static_cast<double>(L) * tot);
+        fac_out[kidx] = vlist ? tot : 1.0 / (static_cast<double>(L) * tot);
     }
 }
 
@@ -197,7 +199,20 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
     g_gl_uploaded = true;
     // a tabulated window is only piecewise cubic: more panels
     const int panels = (window == NFFTBL_WIN_TABLE) ? kTablePanels : 96;
-    window_factor_kernel<<<M, 256, 0, s>>>(with_sinc, window, L, M, m, beta, table, table_n, panels, fac64_out);
+    window_factor_kernel<<<M, 256, 0, s>>>(with_sinc, window, L, M, m, beta, table, table_n, panels, nullptr,
+                                           fac64_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_transform(int with_sinc, int window, int L, int m, double beta, const double* table,
+                                    int table_n, const double* v, int n, double* out, cudaStream_t s) {
+    static GLRule rule;
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_gl_x, rule.x, sizeof(rule.x), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_gl_w, rule.w, sizeof(rule.w), 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaSuccess;
+    const int panels = (window == NFFTBL_WIN_TABLE) ? kTablePanels : 96;
+    window_factor_kernel<<<n, 256, 0, s>>>(with_sinc, window, L, 0, m, beta, table, table_n, panels, v, out);
     return cudaGetLastError();
 }
 
