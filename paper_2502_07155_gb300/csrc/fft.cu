@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
         for (int b = tid; b < W * nb; b += blockDim.x) {
             const int w = b / nb;
             const int i = b - w * nb;
-            const int k = i % span;
+            const int k = (span & (span - 1)) ? i % span : (i & (span - 1));
             const CT* s = src + w * pitch;
             CT* dd = dst + w * pitch;
             const int obase = (i - k) * r + k;
