@@ -140,6 +140,8 @@ def run_paper(args):
     Ms = [20, 40, 80, 100, 200, 400, 600, 800, 1000]
     ex = {str(M): {f"{meth}_{prec}": example51_errors(M, 5, prec, meth) for meth in ("shannon", "classic")
                    for prec in ("f64", "f32")} for M in Ms}
+    for M in Ms:   # ablation: D = I (Section 5's |I_L| psi_hat ~ 1)
+        ex[str(M)]["shannon_f64_D=I"] = example51_errors(M, 5, "f64", "shannon", precorrect=False)
     beta_sh = float(np.pi * 5 * 0.5)
     curves = {}
     for name, kw in [("shannon_full", dict(interval="full")), ("shannon_trunc", dict(interval="trunc")),

@@ -92,6 +92,9 @@ typedef struct {
                                nfftbl_set_nodes (N * d * 2m values in the plan precision,
                                rows padded to 4); 0 (default) evaluates them in every
                                transform, which is faster on GB300 for the sinh window  */
+    int precorrect;         /* 1 (default): D_psihat = diag(1/(|I_L| psi_hat(k))) of Eq. 4.9
+                               (D of Eq. 2.2); 0: D = I, the approximation of Section 5
+                               that uses |I_L| psi_hat(k) ~ 1 (an ablation)             */
 } nfftbl_opts;
 
 /* Fill *opts with the defaults listed above. */

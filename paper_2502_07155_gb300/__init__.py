@@ -53,7 +53,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("method", ctypes.c_int), ("beta", ctypes.c_double),
                 ("batch", ctypes.c_int), ("table", ctypes.POINTER(ctypes.c_double)),
                 ("table_len", ctypes.c_int), ("tile", ctypes.c_int * 3), ("nodes_per_item", ctypes.c_int),
-                ("factors", ctypes.c_int)]
+                ("factors", ctypes.c_int), ("precorrect", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -164,13 +164,14 @@ class Plan:
     ``precision`` ('f32' | 'f32c' | 'f64'), ``method`` ('shannon' |
     'classic'), ``beta`` (None = default), ``batch``, ``table`` (values on
     u in [0, 1] for the table window), ``tile``, ``nodes_per_item``,
-    ``factors`` (keep the d x 2m window factors per node from set_nodes).
+    ``factors`` (keep the d x 2m window factors per node from set_nodes),
+    ``precorrect`` (False: D = I, Section 5's approximation |I_L| psi_hat ~ 1).
     """
 
     def __init__(self, d: int, M, sigma: float = 2.0, m: int = 6, window: str = "sinh",
                  precision: str = "f32", method: str = "shannon", beta: float | None = None,
                  batch: int = 1, table=None, tile=None, nodes_per_item: int | None = None,
-                 factors: bool = False):
+                 factors: bool = False, precorrect: bool = True):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("nfftbl needs a CUDA device; there is no CPU fallback")
@@ -198,6 +199,7 @@ class Plan:
         if nodes_per_item:
             o.nodes_per_item = int(nodes_per_item)
         o.factors = 1 if factors else 0
+        o.precorrect = 1 if precorrect else 0
         Marr = (ctypes.c_int * 3)(*(Ms + [0] * (3 - d)))
         h = ctypes.c_void_p()
         st = self._lib.nfftbl_plan(ctypes.byref(h), d, Marr, float(sigma), int(m), _WINDOWS[window], ctypes.byref(o))

@@ -360,6 +360,7 @@ void nfftbl_default_opts(nfftbl_opts* o) {
     o->beta = 0.0;
     o->batch = 1;
     o->factors = 0;
+    o->precorrect = 1;
 }
 
 nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m, int window,
@@ -378,6 +379,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     if (o.precision < 0 || o.precision > 2) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown precision");
     if (o.method < 0 || o.method > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown method");
     if (o.factors < 0 || o.factors > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "factors must be 0 or 1");
+    if (o.precorrect < 0 || o.precorrect > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "precorrect must be 0 or 1");
     if (o.batch < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "batch must be >= 1");
     if (window == NFFTBL_WIN_TABLE && (!o.table || o.table_len < 3))
         return plan_fail(nullptr, NFFTBL_EINVAL, "table window needs a table of >= 3 values");
@@ -463,6 +465,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     p->batch = o.batch;
     p->nodes_per_item = o.nodes_per_item > 0 ? o.nodes_per_item : 1024;
     p->store_factors = o.factors;
+    p->precorrect = o.precorrect;
     p->geom = g;
     p->smem_optin = optin;
     p->key_bits = key_bits;
@@ -513,10 +516,20 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
         if ((st = ensure_buf(p, p->fac64[t], M[t] * sizeof(double))) != NFFTBL_OK) return plan_fail(p, st, "");
         if ((st = ensure_buf(p, p->facT[t], M[t] * (dbl ? 8 : 4))) != NFFTBL_OK) return plan_fail(p, st, "");
         if ((st = ensure_buf(p, p->tw[t], L[t] * complex_bytes(p))) != NFFTBL_OK) return plan_fail(p, st, "");
-        if ((st = check_cuda(p, launch_window_factors(p->method == NFFTBL_SHANNON, window, L[t], M[t], m, beta,
-                                                      tab64, tab_n, static_cast<double*>(p->fac64[t].p), s0),
-                             "window factors")) != NFFTBL_OK)
-            return plan_fail(p, st, "");
+        if (p->precorrect) {
+            if ((st = check_cuda(p, launch_window_factors(p->method == NFFTBL_SHANNON, window, L[t], M[t], m, beta,
+                                                          tab64, tab_n, static_cast<double*>(p->fac64[t].p), s0),
+                                 "window factors")) != NFFTBL_OK)
+                return plan_fail(p, st, "");
+        } else {
+            // D = I (Section 5: |I_L| psi_hat(k) ~ 1, so 1/(|I_L| psi_hat) ~ 1): factor 1
+            const std::vector<double> inv(M[t], 1.0);
+            if ((st = check_cuda(p, cudaMemcpyAsync(p->fac64[t].p, inv.data(), M[t] * sizeof(double),
+                                                    cudaMemcpyHostToDevice, s0),
+                                 "factors")) != NFFTBL_OK)
+                return plan_fail(p, st, "");
+            if ((st = check_cuda(p, cudaStreamSynchronize(s0), "factors")) != NFFTBL_OK) return plan_fail(p, st, "");
+        }
         if ((st = check_cuda(p, launch_cast_factors(static_cast<double*>(p->fac64[t].p), M[t], p->facT[t].p, dbl, s0),
                              "factor cast")) != NFFTBL_OK)
             return plan_fail(p, st, "");
@@ -758,6 +771,7 @@ nfftbl_status nfftbl_set_window_table(nfftbl_plan_t p, const double* table_dev, 
                                               static_cast<float4*>(p->table_coef.p), p->stream),
                          "table cast")) != NFFTBL_OK)
         return st;
+    if (!p->precorrect) return p->wfac_valid ? compute_factors(p) : NFFTBL_OK;   // D = I: no psi_hat
     for (int t = 0; t < p->d; ++t) {
         if ((st = check_cuda(p, launch_window_factors(1, NFFTBL_WIN_TABLE, p->L[t], p->M[t], p->m, p->beta,
                                                       static_cast<const double*>(t64), table_len - 1,
@@ -780,8 +794,8 @@ nfftbl_status nfftbl_window_loss_grad(nfftbl_plan_t p, const void* fhat_dev, con
     nfftbl_status st = ready(p);
     if (st != NFFTBL_OK) return st;
     if (!fhat_dev || !y_dev || !grad_table_dev || !loss_dev) return fail(p, NFFTBL_EINVAL, "NULL pointer");
-    if (p->window != NFFTBL_WIN_TABLE || p->method != NFFTBL_SHANNON)
-        return fail(p, NFFTBL_ESTATE, "window gradients need a Shannon plan with a table window");
+    if (p->window != NFFTBL_WIN_TABLE || p->method != NFFTBL_SHANNON || !p->precorrect)
+        return fail(p, NFFTBL_ESTATE, "window gradients need a precorrected Shannon plan with a table window");
     if (p->precision == NFFTBL_F64 || p->d > 2)
         return fail(p, NFFTBL_EUNSUPPORTED, "window gradients are built for FP32 plans with d <= 2");
     const long long B = p->batch, N = p->N;

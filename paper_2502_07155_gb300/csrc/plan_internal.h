@@ -212,6 +212,7 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf hist;               // radix sort block histograms
     nfftbl::DeviceBuf wfac;               // stored window factors (step 0b, tensor-product form)
     int store_factors = 1;
+    int precorrect = 1;                   // 0: D = I (Section 5's approximation)
     bool wfac_valid = false;
     nfftbl::DeviceBuf table_coef;         // FP32 table window: float4 cubic coefficients per interval
     nfftbl::DeviceBuf scan_tmp;           // per-tile sums of the multi-block scan

@@ -27,7 +27,7 @@ from . import Plan
 
 
 def example51_errors(M: int, m: int = 5, precision: str = "f64", method: str = "shannon",
-                     beta: float | None = None) -> float:
+                     beta: float | None = None, precorrect: bool = True) -> float:
     """max_j |f_j - sinc^2(M pi x_j / 2)| of one forward transform (d = 1,
     sigma = 2) on the N = M/2 scaled Chebyshev nodes of Example 5.1."""
     import torch
@@ -36,7 +36,7 @@ def example51_errors(M: int, m: int = 5, precision: str = "f64", method: str = "
     fh = ((2.0 / M) * W.triangle(M, 1)).astype(np.complex128)[None]
     rdt = torch.float64 if precision == "f64" else torch.float32
     cdt = torch.complex128 if precision == "f64" else torch.complex64
-    plan = Plan(1, M, 2.0, m, precision=precision, method=method, beta=beta)
+    plan = Plan(1, M, 2.0, m, precision=precision, method=method, beta=beta, precorrect=precorrect)
     plan.set_nodes(torch.from_numpy(x).to("cuda", rdt))
     f = plan.forward(torch.from_numpy(fh).to("cuda", cdt)).to(torch.complex128).cpu().numpy()[0]
     plan.close()

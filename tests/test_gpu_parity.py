@@ -202,6 +202,33 @@ def test_general_L_parity(d, M, m, prec, method):
     assert rel_l2(h, O.adjoint(op, g, x)) < TOL[prec]
 
 
+@pytest.mark.parametrize("d,prec,method", [(1, "f64", "shannon"), (2, "f64", "shannon"), (2, "f32", "classic"),
+                                           (3, "f32", "shannon")])
+def test_without_precorrection(d, prec, method):
+    """precorrect=False: D = I (Section 5's approximation |I_L| psi_hat ~ 1,
+    so 1/(|I_L| psi_hat) ~ 1): factors 1, forward and adjoint against the
+    oracle run with the same factors, and close to the precorrected result
+    (D_psihat differs from I by the window's ripple in the pass band)."""
+    batch = 2
+    M0, m0, N0, npi0 = SHAPES[d]
+    plan = nb.Plan(d, M0, 2.0, m0, precision=prec, method=method, batch=batch, precorrect=False)
+    x = W.nodes_uniform(N0, d, dtype=RDT[prec], seed=6)
+    plan.set_nodes(to_dev(x))
+    for t in range(d):
+        np.testing.assert_array_equal(plan.factors(t), np.ones(plan.M[t]))
+    op = oracle_plan(plan)
+    fac = [np.ones(plan.M[t]) for t in range(d)]
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+    g = W.adjoint_input(N0, batch=batch, dtype=CDT[prec])
+    f = to_host(plan.forward(to_dev(fh)))
+    assert rel_l2(f, O.forward(op, fh, x, fac)) < TOL[prec]
+    assert rel_l2(to_host(plan.adjoint(to_dev(g))), O.adjoint(op, g, x, fac)) < TOL[prec]
+    # for the Shannon method D_psihat differs from I by the pass-band ripple of
+    # psi_hat only (the classical window's L phi_hat is not close to 1)
+    if method == "shannon":
+        assert rel_l2(f, O.forward(op, fh, x)) < 1e-2
+
+
 def test_general_L_rejects_other_primes():
     with pytest.raises(nb.NfftblError) as e:
         nb.Plan(1, 14, 2.0, 3)        # L = 28 = 2^2 7
