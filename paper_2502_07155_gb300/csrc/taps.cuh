@@ -1,19 +1,23 @@
 // Short-sum kernels over binned nodes: interpolation (Algorithm 4.2 step 3,
 // Eq. 4.8), spreading (its transpose Psi^T, the first factor of the
-// adjoint) and the node derivative of the short sums.
+// adjoint), the node derivative of the short sums and the optional stored
+// window factors (step 0b in tensor-product form).
 //
 // Work decomposition: one work item = one tile of T_0 x .. x T_{d-1} grid
-// cells and up to K of its nodes (sorted by cell).  A CTA stages the box of
-// grid values the tile's nodes can reach -- the tile plus its m-halo -- in
-// shared memory (TMA tiled load; out-of-range cells are zero-filled by the
-// copy engine, which is exactly the zero extension of the Shannon method
-// outside I_L) and every thread evaluates one node at a time.
+// cells and up to K of its nodes (sorted by cell).  The box of grid values
+// the tile's nodes can reach -- the tile plus its m-halo -- lives in shared
+// memory: interp_kernel / node_grad_kernel stage it with one TMA tiled load
+// (out-of-range cells are zero-filled by the copy engine, which is exactly
+// the zero extension of the Shannon method outside I_L) and evaluate one
+// node per thread; the spread kernels (spread1/2/3_kernel) accumulate it in
+// exact fixed point, warps walking the item's nodes, and store it for the
+// ordered flush (gather_kernel).
 //
-// Per node and dimension t: u = L_t x_t (exact for L_t = 2^p), cell
-// i = floor(u), tau = u - i in [0, 1).  The 2m taps l = i-m+1 .. i+m (the
-// members of the closed set J_{L,m}(x) with a nonzero window; the ends of
-// the closed set carry phi(+-m/L) = 0) have offsets
-// delta_a = L x - l = tau + m-1-a, and
+// Per node and dimension t: u = L_t x_t (one correctly rounded product,
+// exact for L_t = 2^p), cell i = floor(u), tau = u - i in [0, 1).  The 2m
+// taps l = i-m+1 .. i+m (the members of the closed set J_{L,m}(x) with a
+// nonzero window; the ends of the closed set carry phi(+-m/L) = 0) have
+// offsets delta_a = L x - l = tau + m-1-a, and
 //   sinc(pi delta_a) = (-1)^(m-1-a) sin(pi tau) / (pi delta_a),
 // so one sinpi per node and dimension serves all taps.  The tensor-product
 // kernel psi(x - l/L) = prod_t psi_t is contracted dimension by dimension:
