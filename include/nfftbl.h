@@ -117,7 +117,9 @@ void nfftbl_default_opts(nfftbl_opts* opts);
  * Errors: EINVAL (d, M odd or < 2, sigma < 1, m < 1, 2m >= L_t, batch < 1,
  * bad table or tile, beta <= 0 after defaults), EUNSUPPORTED (L_t not of
  * the form 2^a 3^b 5^c in [16, 4096] -- the FFT's radices --, m outside
- * 2..12, prod L_t > 2^31, a box of tile plus halo beyond shared memory),
+ * 2..12, prod L_t > 2^31, a box of tile plus halo beyond shared memory:
+ * with the smallest tiles this limits d = 3 to m <= 8 in FP64 and m <= 9 in
+ * FP32),
  * ENOMEM, ECUDA.  Tiles are the largest power of two (up to 64 / 32^2 / 8^3
  * for d = 1 / 2 / 3) dividing L_t.  The message of a
  * failed call is available from nfftbl_plan_error().

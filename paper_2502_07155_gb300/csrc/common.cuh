@@ -27,6 +27,19 @@ template <typename T> using C2 = typename Cplx<T>::type;
 template <typename T>
 __device__ __forceinline__ C2<T> cmake(T r, T i) { C2<T> z; z.x = r; z.y = i; return z; }
 
+// acc + v * w componentwise for a pair v and a scalar w.  FP32 pairs take one
+// packed FMA (fma.rn.f32x2, sm_100 and later): each component is an IEEE fma
+// rounded to nearest, so the result equals two fmaf calls bit for bit while
+// issuing one instruction instead of two.
+__device__ __forceinline__ float2 cfma(float2 v, float w, float2 acc) {
+    return __ffma2_rn(v, make_float2(w, w), acc);
+}
+__device__ __forceinline__ double2 cfma(double2 v, double w, double2 acc) {
+    acc.x = fma(v.x, w, acc.x);
+    acc.y = fma(v.y, w, acc.y);
+    return acc;
+}
+
 // One work item of the interpolation / spreading kernels: a tile and a run of
 // its nodes in sorted order.
 struct WorkItem {

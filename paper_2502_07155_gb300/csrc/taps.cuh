@@ -373,6 +373,51 @@ __device__ __forceinline__ void tap_weights_d(T tau, T Lt, const WinParams<T>& w
 // widest aligned vector loads the row length allows (rows start 16-byte
 // aligned when A is a multiple of 4 floats / 2 doubles, 8-byte aligned when
 // A is even).
+// Register sums of one spreading lane over the 2m rows of its column:
+// re[q] += gr w[q], im[q] += gi w[q] for the rows q < nw.  FP32 keeps the
+// rows in pairs so that each update of two rows is one packed FMA (the
+// weights w[q], w[q + 1] are adjacent after a vector load).
+template <typename T, int A>
+struct RowSums {
+    T r[A], i[A];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < A; ++q) r[q] = i[q] = T(0);
+    }
+    __device__ __forceinline__ void add(T gr, T gi, const T (&w)[A], int nw) {
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            if (q < nw) {
+                r[q] += gr * w[q];
+                i[q] += gi * w[q];
+            }
+        }
+    }
+    __device__ __forceinline__ T re(int q) const { return r[q]; }
+    __device__ __forceinline__ T im(int q) const { return i[q]; }
+};
+template <int A>
+struct RowSums<float, A> {
+    static_assert(A % 2 == 0, "rows are summed in pairs");
+    float2 r[A / 2], i[A / 2];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int h = 0; h < A / 2; ++h) r[h] = i[h] = make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void add(float gr, float gi, const float (&w)[A], int nw) {
+#pragma unroll
+        for (int h = 0; h < A / 2; ++h) {
+            if (2 * h < nw) {   // nw is even
+                const float2 wp = make_float2(w[2 * h], w[2 * h + 1]);
+                r[h] = cfma(wp, gr, r[h]);
+                i[h] = cfma(wp, gi, i[h]);
+            }
+        }
+    }
+    __device__ __forceinline__ float re(int q) const { return (q & 1) ? r[q >> 1].y : r[q >> 1].x; }
+    __device__ __forceinline__ float im(int q) const { return (q & 1) ? i[q >> 1].y : i[q >> 1].x; }
+};
+
 template <typename T, int A>
 __device__ __forceinline__ void load_row(const T* __restrict__ src, T (&dst)[A]) {
     if (sizeof(T) == 4 && A % 4 == 0) {
@@ -469,33 +514,24 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
     const int nw = W ? W : nw_rt;
     if (D == 1) {
         const C2<T>* p = box + lb[0];
-        T ar = T(0), ai = T(0);
+        C2<T> acc = cmake<T>(T(0), T(0));
 #pragma unroll
-        for (int a = 0; a < nw; ++a) {
-            const C2<T> v = p[a];
-            ar += v.x * w0[a];
-            ai += v.y * w0[a];
-        }
-        return cmake<T>(ar, ai);
+        for (int a = 0; a < nw; ++a) acc = cfma(p[a], w0[a], acc);
+        return acc;
     } else if (D == 2) {
         const int pitch = g.box[1];
         const C2<T>* p = box + lb[0] * pitch + lb[1];
         if (!comp) {
-            T ar = T(0), ai = T(0);
+            C2<T> acc = cmake<T>(T(0), T(0));
 #pragma unroll 4
             for (int a = 0; a < nw; ++a) {
                 const C2<T>* row = p + a * pitch;
-                T rr = T(0), ri = T(0);
+                C2<T> r = cmake<T>(T(0), T(0));
 #pragma unroll
-                for (int b = 0; b < nw; ++b) {
-                    const C2<T> v = row[b];
-                    rr += v.x * w1[b];
-                    ri += v.y * w1[b];
-                }
-                ar += rr * w0[a];
-                ai += ri * w0[a];
+                for (int b = 0; b < nw; ++b) r = cfma(row[b], w1[b], r);
+                acc = cfma(r, w0[a], acc);
             }
-            return cmake<T>(ar, ai);
+            return acc;
         } else {
             CompAcc<T> acc;
 #pragma unroll 4
@@ -517,26 +553,20 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
         const int p0 = g.box[1] * p1;
         const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
         if (!comp) {
-            T ar = T(0), ai = T(0);
+            C2<T> acc = cmake<T>(T(0), T(0));
             for (int a = 0; a < nw; ++a) {
-                T mr = T(0), mi = T(0);
+                C2<T> mid = cmake<T>(T(0), T(0));
 #pragma unroll 2
                 for (int b = 0; b < nw; ++b) {
                     const C2<T>* row = p + a * p0 + b * p1;
-                    T rr = T(0), ri = T(0);
+                    C2<T> r = cmake<T>(T(0), T(0));
 #pragma unroll
-                    for (int c = 0; c < nw; ++c) {
-                        const C2<T> v = row[c];
-                        rr += v.x * w2[c];
-                        ri += v.y * w2[c];
-                    }
-                    mr += rr * w1[b];
-                    mi += ri * w1[b];
+                    for (int c = 0; c < nw; ++c) r = cfma(row[c], w2[c], r);
+                    mid = cfma(r, w1[b], mid);
                 }
-                ar += mr * w0[a];
-                ai += mi * w0[a];
+                acc = cfma(mid, w0[a], acc);
             }
-            return cmake<T>(ar, ai);
+            return acc;
         } else {
             CompAcc<T> acc;
             for (int a = 0; a < nw; ++a) {
@@ -570,7 +600,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
                                                 const WinParams<T>& wp, int nw_rt) {
     const int nw = W ? W : nw_rt;
     const int m = nw / 2;
-    T ar = T(0), ai = T(0);
+    C2<T> acc = cmake<T>(T(0), T(0));
     if (D == 2) {
         const int pitch = g.box[1];
         const C2<T>* p = box + lb[0] * pitch + lb[1];
@@ -578,17 +608,11 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         for (int a = 0; a < nw; ++a) {
             const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
             const C2<T>* row = p + a * pitch;
-            T rr = T(0), ri = T(0);
+            C2<T> r = cmake<T>(T(0), T(0));
 #pragma unroll
-            for (int b = 0; b < TapN<W>::A; ++b) {
-                if (b < nw) {
-                    const C2<T> v = row[b];
-                    rr += v.x * w1[b];
-                    ri += v.y * w1[b];
-                }
-            }
-            ar += rr * w0a;
-            ai += ri * w0a;
+            for (int b = 0; b < TapN<W>::A; ++b)
+                if (b < nw) r = cfma(row[b], w1[b], r);
+            acc = cfma(r, w0a, acc);
         }
     } else {
         const int p1 = g.box[2];
@@ -596,27 +620,20 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
         for (int a = 0; a < nw; ++a) {
             const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
-            T mr = T(0), mi = T(0);
+            C2<T> mid = cmake<T>(T(0), T(0));
 #pragma unroll 2
             for (int b = 0; b < nw; ++b) {
                 const C2<T>* row = p + a * p0 + b * p1;
-                T rr = T(0), ri = T(0);
+                C2<T> r = cmake<T>(T(0), T(0));
 #pragma unroll
-                for (int c = 0; c < TapN<W>::A; ++c) {
-                    if (c < nw) {
-                        const C2<T> v = row[c];
-                        rr += v.x * w2[c];
-                        ri += v.y * w2[c];
-                    }
-                }
-                mr += rr * w1[b];
-                mi += ri * w1[b];
+                for (int c = 0; c < TapN<W>::A; ++c)
+                    if (c < nw) r = cfma(row[c], w2[c], r);
+                mid = cfma(r, w1[b], mid);
             }
-            ar += mr * w0a;
-            ai += mi * w0a;
+            acc = cfma(mid, w0a, acc);
         }
     }
-    return cmake<T>(ar, ai);
+    return acc;
 }
 
 // Copy n = 2m (n <= A) window factors from src to dst with the widest
@@ -1048,15 +1065,14 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                 for (int bb = 0; bb < nb; ++bb) {
                     unsigned char* bx = reinterpret_cast<unsigned char*>(boxu + static_cast<size_t>(bb) * slot * 2);
                     int seg = -1, seg_lb0 = 0, col = 0;
-                    T ar[A], ai[A];
-#pragma unroll
-                    for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                    RowSums<T, A> acc;
+                    acc.zero();
                     auto flush = [&]() {
                         if (col < box1) {
 #pragma unroll
                             for (int q = 0; q < A; ++q) {
                                 if (q < nw) {
-                                    FixedCell<T>::add(bx, (seg_lb0 + q) * box1 + col, slot, ar[q], ai[q]);
+                                    FixedCell<T>::add(bx, (seg_lb0 + q) * box1 + col, slot, acc.re(q), acc.im(q));
                                 }
                             }
                         }
@@ -1121,8 +1137,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                                 seg = key;
                                 seg_lb0 = key & 0xFFFF;
                                 col = (key >> 16) * S + lane;
-#pragma unroll
-                                for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                                acc.zero();
                             }
                             const int t = lane - kt.y;
                             const bool in = static_cast<unsigned>(t) < static_cast<unsigned>(nw);
@@ -1131,13 +1146,7 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                             const T gr = g.x * wf, gi = g.y * wf;
                             T w0r[A];
                             load_row<T, A>(row, w0r);
-#pragma unroll
-                            for (int q = 0; q < A; ++q) {
-                                if (q < nw) {
-                                    ar[q] += gr * w0r[q];
-                                    ai[q] += gi * w0r[q];
-                                }
-                            }
+                            acc.add(gr, gi, w0r, nw);
                         };
                         int k = 0;
 #pragma unroll 1
@@ -1157,15 +1166,8 @@ __global__ void __launch_bounds__(kTapThreads, sizeof(T) == 4 ? 3 : 1) spread2_k
                                 T wa[A], wb[A];
                                 load_row<T, A>(ra, wa);
                                 load_row<T, A>(rb, wb);
-#pragma unroll
-                                for (int q = 0; q < A; ++q) {
-                                    if (q < nw) {
-                                        ar[q] += gra * wa[q];
-                                        ai[q] += gia * wa[q];
-                                        ar[q] += grb * wb[q];
-                                        ai[q] += gib * wb[q];
-                                    }
-                                }
+                                acc.add(gra, gia, wa, nw);
+                                acc.add(grb, gib, wb, nw);
                             } else {
                                 one(ra);
                                 one(rb);
@@ -1274,29 +1276,23 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                                 const bool valid = pp < npairs;
                                 const int a1 = valid ? pp / nw : 0;
                                 const int a2 = valid ? pp - a1 * nw : 0;
-                                T ar[A], ai[A];
-#pragma unroll
-                                for (int q = 0; q < A; ++q) ar[q] = ai[q] = T(0);
+                                RowSums<T, A> acc;
+                                acc.zero();
                                 for (int kk = k; kk < k1; ++kk) {
                                     const T* row = s_tab + kk * RS;
                                     const T w12 = row[A + a1] * row[2 * A + a2];
                                     const T gr = row[3 * A] * w12, gi = row[3 * A + 1] * w12;
                                     T w0r[A];
                                     load_row<T, A>(row, w0r);
-#pragma unroll
-                                    for (int q = 0; q < A; ++q) {
-                                        if (q < nw) {
-                                            ar[q] += gr * w0r[q];
-                                            ai[q] += gi * w0r[q];
-                                        }
-                                    }
+                                    acc.add(gr, gi, w0r, nw);
                                 }
                                 if (valid) {
                                     const int base = (lb0 * bx1 + lb1 + a1) * bx2 + lb2 + a2;
                                     const int pitch0 = bx1 * bx2;
 #pragma unroll
                                     for (int q = 0; q < A; ++q)
-                                        if (q < nw) FixedCell<T>::add(bx, base + q * pitch0, box_cells, ar[q], ai[q]);
+                                        if (q < nw)
+                                            FixedCell<T>::add(bx, base + q * pitch0, box_cells, acc.re(q), acc.im(q));
                                 }
                             }
                             k = k1;
@@ -1398,13 +1394,10 @@ __global__ void __launch_bounds__(kTapThreads) spread1_kernel(const TapArgs<T> a
                             const int lb0 = s_lb[jlo];
                             for (int bb = 0; bb < nb; ++bb) {
                                 const CT* gg = s_g + bb * sub;
-                                T ar = T(0), ai = T(0);
-                                for (int j = jlo + rg; j < jhi; j += G) {
-                                    const T wv = s_w[static_cast<size_t>(j) * A + c];
-                                    ar += gg[j].x * wv;
-                                    ai += gg[j].y * wv;
-                                }
-                                FixedCell<T>::add(boxc + static_cast<size_t>(bb) * slot * 16, lb0 + c, slot, ar, ai);
+                                CT acc = cmake<T>(T(0), T(0));
+                                for (int j = jlo + rg; j < jhi; j += G)
+                                    acc = cfma(gg[j], s_w[static_cast<size_t>(j) * A + c], acc);
+                                FixedCell<T>::add(boxc + static_cast<size_t>(bb) * slot * 16, lb0 + c, slot, acc.x, acc.y);
                             }
                         }
                     }

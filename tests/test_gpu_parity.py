@@ -357,3 +357,54 @@ def test_adjoint_dense_cells(d, prec, method):
     assert rel_l2(h, ref) < TOL[prec]
     f = to_host(plan.forward(to_dev(W.fhat_gaussian(plan.M, dtype=CDT[prec]))))
     assert np.all(np.isfinite(f))
+
+
+# --------------------------------------------------------------------------- truncation m chosen at run time
+
+# Truncations outside the compile-time set {2, 3, 4, 5, 6, 8} run the kernels
+# that take m as an argument (tap arrays of length 24, loops bounded by 2m).
+RUNTIME_M = [
+    (1, 256, 12, "f64", "shannon", "sinh", False),
+    (1, 256, 9, "f32", "classic", "sinh", False),
+    (2, 64, 7, "f32", "shannon", "sinh", False),
+    (2, 64, 10, "f64", "classic", "sinh", False),
+    (2, 64, 7, "f64", "shannon", "ckb", False),
+    (2, 64, 11, "f32", "shannon", "sinh", True),      # stored window factors
+    (3, 32, 7, "f32", "shannon", "sinh", False),
+    (3, 32, 9, "f32", "classic", "sinh", False),
+    (3, 32, 7, "f64", "classic", "sinh", True),
+]
+
+
+@pytest.mark.parametrize("d,M,m,prec,method,window,factors", RUNTIME_M)
+def test_runtime_m_parity(d, M, m, prec, method, window, factors):
+    """Forward, adjoint (Eq. 4.11 and its transpose) and the node gradient
+    against the oracle for truncations without a compiled kernel; batch 2 and
+    small work items so that several items share a tile."""
+    batch, N = 2, 1500
+    plan = nb.Plan(d, M, 2.0, m, window=window, precision=prec, method=method, batch=batch,
+                   nodes_per_item=96, factors=factors)
+    x = W.nodes_uniform(N, d, dtype=RDT[prec], seed=5)
+    plan.set_nodes(to_dev(x))
+    op = oracle_plan(plan)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec])
+    g = W.adjoint_input(N, batch=batch, dtype=CDT[prec])
+    f = to_host(plan.forward(to_dev(fh)))
+    assert rel_l2(f, O.forward(op, fh, x)) < TOL[prec]
+    h = to_host(plan.adjoint(to_dev(g)))
+    plan.sync()
+    assert rel_l2(h, O.adjoint(op, g, x)) < TOL[prec]
+    gx = to_host(plan.node_grad(to_dev(fh), to_dev(g)))
+    plan.sync()
+    assert rel_l2(gx, O.node_grad(op, fh, x, g)) < (1e-10 if prec == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec,m", [("f64", 9), ("f32", 10)])
+def test_runtime_m_box_too_large_is_a_plan_error(prec, m):
+    """d = 3 with a truncation whose smallest spreading box and node tables
+    exceed the shared memory of one block: plan creation fails with
+    EUNSUPPORTED instead of launching (FP64 supports m <= 8 at d = 3, FP32
+    m <= 9)."""
+    with pytest.raises(nb.NfftblError) as e:
+        nb.Plan(3, 32, 2.0, m, precision=prec)
+    assert e.value.name == "EUNSUPPORTED"
