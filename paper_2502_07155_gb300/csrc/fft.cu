@@ -237,6 +237,222 @@ __global__ void __launch_bounds__(kFftThreads) fft_pass_kernel(const C2<T>* __re
     }
 }
 
+constexpr int ilog2_c(int v) { return v <= 1 ? 0 : 1 + ilog2_c(v >> 1); }
+
+// ---------------------------------------------------------------------------
+// Power-of-two lengths: the same pass with L a compile-time constant, radix-8
+// Stockham stages (then one radix-4 or radix-2 stage), shifts instead of
+// divisions.  A pass is bound by the latency of each thread's instruction
+// chain (few lines per pass, few warps per SM), so fewer stages and
+// instructions per element shorten it directly.
+
+// 8-point DFT of c (forward pass: e^{+2 pi i jq/8}, adjoint: e^{-2 pi i jq/8})
+// as two 4-point DFTs of the sums c_j + c_{j+4} (even outputs) and of the
+// differences times e^{+-2 pi i j/8} (odd outputs).
+template <typename T, bool ADJ>
+__device__ __forceinline__ void dft8(C2<T> (&c)[8]) {
+    using CT = C2<T>;
+    const T h = static_cast<T>(0.70710678118654752440);
+    auto rot = [](CT v) { return ADJ ? cmake<T>(v.y, -v.x) : cmake<T>(-v.y, v.x); };
+    auto add = [](CT a, CT b) { return cmake<T>(a.x + b.x, a.y + b.y); };
+    auto sub = [](CT a, CT b) { return cmake<T>(a.x - b.x, a.y - b.y); };
+    CT a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        a[j] = add(c[j], c[j + 4]);
+        b[j] = sub(c[j], c[j + 4]);
+    }
+    // b1 *= (1 +- i)/sqrt 2, b2 *= +-i, b3 *= (-1 +- i)/sqrt 2
+    b[1] = ADJ ? cmake<T>(h * (b[1].x + b[1].y), h * (b[1].y - b[1].x))
+               : cmake<T>(h * (b[1].x - b[1].y), h * (b[1].x + b[1].y));
+    b[2] = rot(b[2]);
+    b[3] = ADJ ? cmake<T>(h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y))
+               : cmake<T>(-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y));
+    auto dft4 = [&](const CT (&x)[4], CT& y0, CT& y1, CT& y2, CT& y3) {
+        const CT s02 = add(x[0], x[2]), d02 = sub(x[0], x[2]);
+        const CT s13 = add(x[1], x[3]), d13 = rot(sub(x[1], x[3]));
+        y0 = add(s02, s13);
+        y1 = add(d02, d13);
+        y2 = sub(s02, s13);
+        y3 = sub(d02, d13);
+    };
+    dft4(a, c[0], c[2], c[4], c[6]);
+    dft4(b, c[1], c[3], c[5], c[7]);
+}
+
+// One Stockham stage of radix R and span S over W lines of length L: butterfly
+// i (k = i mod S) reads i + j L/R, multiplies input j by w^(j k L/(R S)) and
+// writes output q to (i - k) R + k + q S.
+template <typename T, bool ADJ, int L, int R, int S>
+__device__ __forceinline__ void pow2_stage(const C2<T>* __restrict__ src, C2<T>* __restrict__ dst,
+                                           const C2<T>* __restrict__ twd, int W, int pitch) {
+    using CT = C2<T>;
+    constexpr int NB = L / R;
+    constexpr int LG_NB = ilog2_c(NB);
+    constexpr int TSTEP = L / (R * S);
+    for (int b = threadIdx.x; b < W * NB; b += blockDim.x) {
+        const int w = b >> LG_NB;
+        const int i = b & (NB - 1);
+        const int k = i & (S - 1);
+        const CT* s = src + w * pitch;
+        CT* dd = dst + w * pitch + (i - k) * R + k;
+        CT c[8];
+#pragma unroll
+        for (int j = 0; j < R; ++j) c[j] = s[i + j * NB];
+        if (S > 1) {
+            const int e = k * TSTEP;
+#pragma unroll
+            for (int j = 1; j < R; ++j) c[j] = ADJ ? cmulc<T>(c[j], twd[j * e]) : cmul<T>(c[j], twd[j * e]);
+        }
+        auto rot = [](CT v) { return ADJ ? cmake<T>(v.y, -v.x) : cmake<T>(-v.y, v.x); };
+        if constexpr (R == 8) {
+            dft8<T, ADJ>(c);
+        } else if constexpr (R == 4) {
+            const CT a0 = cmake<T>(c[0].x + c[2].x, c[0].y + c[2].y);
+            const CT a1 = cmake<T>(c[0].x - c[2].x, c[0].y - c[2].y);
+            const CT a2 = cmake<T>(c[1].x + c[3].x, c[1].y + c[3].y);
+            const CT a3 = rot(cmake<T>(c[1].x - c[3].x, c[1].y - c[3].y));
+            c[0] = cmake<T>(a0.x + a2.x, a0.y + a2.y);
+            c[1] = cmake<T>(a1.x + a3.x, a1.y + a3.y);
+            c[2] = cmake<T>(a0.x - a2.x, a0.y - a2.y);
+            c[3] = cmake<T>(a1.x - a3.x, a1.y - a3.y);
+        } else {
+            const CT a0 = c[0];
+            c[0] = cmake<T>(a0.x + c[1].x, a0.y + c[1].y);
+            c[1] = cmake<T>(a0.x - c[1].x, a0.y - c[1].y);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) dd[q * S] = c[q];
+    }
+}
+
+// Stages of span S, S R, ... up to L (radix 8 while 8 divides L / S).
+template <typename T, bool ADJ, int L, int S>
+__device__ __forceinline__ void pow2_stages(C2<T>*& src, C2<T>*& dst, const C2<T>* twd, int W, int pitch) {
+    if constexpr (S < L) {
+        constexpr int REM = L / S;
+        constexpr int R = (REM % 8 == 0) ? 8 : (REM % 4 == 0) ? 4 : 2;
+        pow2_stage<T, ADJ, L, R, S>(src, dst, twd, W, pitch);
+        __syncthreads();
+        C2<T>* tmp = src;
+        src = dst;
+        dst = tmp;
+        pow2_stages<T, ADJ, L, S * R>(src, dst, twd, W, pitch);
+    }
+}
+
+// The pass of fft_pass_kernel for L = 2^LG; W (lines per CTA) = 2^lgW.
+template <typename T, bool ADJ, int LG>
+__global__ void __launch_bounds__(kFftThreads) fft_pow2_kernel(const C2<T>* __restrict__ in, C2<T>* __restrict__ out,
+                                                               long long outer, int inner, int M, int lgW,
+                                                               const T* __restrict__ fac,
+                                                               const C2<T>* __restrict__ tw) {
+    using CT = C2<T>;
+    constexpr int L = 1 << LG;
+    constexpr int pitch = L + 1;
+    const int W = 1 << lgW;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    CT* bufA = reinterpret_cast<CT*>(sm_raw);
+    CT* bufB = bufA + W * pitch;
+    CT* twd = bufB + W * pitch;
+    const int tid = threadIdx.x;
+    const int bd = blockDim.x;
+    for (int j = tid; j < L; j += bd) twd[j] = tw[j];
+
+    const int n_in = ADJ ? L : M;
+    const int n_out = ADJ ? M : L;
+    long long o0 = 0;
+    int i0 = 0, nl = W;
+    if (inner == 1) {
+        o0 = static_cast<long long>(blockIdx.x) << lgW;
+        nl = static_cast<int>((outer - o0 < W) ? (outer - o0) : W);
+    } else {
+        const int per = inner >> lgW;
+        o0 = blockIdx.x / per;
+        i0 = (blockIdx.x - static_cast<int>(o0) * per) << lgW;
+    }
+    // element idx of this CTA's W x n lines -> (line w, position p)
+    auto split = [&](int idx, int n, int& w, int& p) {
+        if (inner == 1) {
+            w = (W == 1) ? 0 : idx / n;
+            p = idx - w * n;
+        } else {
+            p = idx >> lgW;
+            w = idx & (W - 1);
+        }
+    };
+
+    // ---- load (zero-padding, precorrection and centring as in fft_pass_kernel)
+    if (!ADJ) {
+        const int zlo = M / 2, zhi = L - M / 2;
+        const int nz = zhi - zlo;
+        for (int idx = tid; idx < W * nz; idx += bd) {
+            const int w = (W == 1) ? 0 : idx / nz;
+            bufA[w * pitch + zlo + idx - w * nz] = cmake<T>(T(0), T(0));
+        }
+    }
+    constexpr int kBatch = 8;
+    for (int idx0 = 0; idx0 < W * n_in; idx0 += kBatch * bd) {
+        CT v[kBatch];
+        T f[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = idx0 + u * bd + tid;
+            v[u] = cmake<T>(T(0), T(0));
+            f[u] = T(1);
+            if (idx < W * n_in) {
+                int w, p;
+                split(idx, n_in, w, p);
+                const long long g = (inner == 1) ? (o0 + w) * n_in + p
+                                                 : (o0 * n_in + p) * static_cast<long long>(inner) + i0 + w;
+                if (w < nl) v[u] = in[g];
+                if (!ADJ) f[u] = fac[p];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = idx0 + u * bd + tid;
+            if (idx < W * n_in) {
+                int w, p;
+                split(idx, n_in, w, p);
+                int q = p;
+                CT val = v[u];
+                if (!ADJ) {
+                    val.x *= f[u];
+                    val.y *= f[u];
+                    q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+                }
+                bufA[w * pitch + q] = val;
+            }
+        }
+    }
+    __syncthreads();
+
+    CT* src = bufA;
+    CT* dst = bufB;
+    pow2_stages<T, ADJ, L, 1>(src, dst, twd, W, pitch);
+
+    // ---- store
+    for (int idx = tid; idx < W * n_out; idx += bd) {
+        int w, p;
+        split(idx, n_out, w, p);
+        if (w >= nl) continue;
+        const long long g = (inner == 1) ? (o0 + w) * n_out + p
+                                         : (o0 * n_out + p) * static_cast<long long>(inner) + i0 + w;
+        CT v;
+        if (!ADJ) {
+            v = src[w * pitch + p];
+        } else {
+            const int q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
+            v = src[w * pitch + q];
+            const T f = fac[p];
+            v.x *= f;
+            v.y *= f;
+        }
+        out[g] = v;
+    }
+}
+
 template <typename T>
 size_t fft_smem(int L, int W) {
     return (2 * static_cast<size_t>(W) * (L + 1) + L) * sizeof(C2<T>);
@@ -249,7 +465,10 @@ template <typename T>
 int choose_lines(int L, long long lines, long long inner, int num_sms) {
     int W = 16;
     while (W > 1 && (fft_smem<T>(L, W) > 64 * 1024 || lines / W < 4LL * num_sms)) W >>= 1;
-    if (inner > 1) W = static_cast<int>(std::min<long long>(W, inner));
+    if (inner > 1) {   // the strided passes take inner / W CTAs per outer index: W must divide inner
+        W = static_cast<int>(std::min<long long>(W, inner));
+        while (W > 1 && inner % W != 0) W >>= 1;
+    }
     return W;
 }
 
@@ -267,18 +486,47 @@ nfftbl_status run_pass(nfftbl_plan_s* p, const void* in, void* out, int t) {
     for (int s = t + 1; s < p->d; ++s) inner *= p->L[s];
     const int L = p->L[t], M = p->M[t];
     const int W = choose_lines<T>(L, outer * inner, inner, p->num_sms);
-    const int threads = fft_threads(L, W);
     const size_t smem = fft_smem<T>(L, W);
+    long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
+    const C2<T>* src = static_cast<const C2<T>*>(in);
+    C2<T>* dst = static_cast<C2<T>*>(out);
+    const T* fac = static_cast<const T*>(p->facT[t].p);
+    const C2<T>* tw = static_cast<const C2<T>*>(p->tw[t].p);
+    if ((L & (L - 1)) == 0) {   // power of two (16 .. 4096): compile-time length, radix-8 stages
+        void (*kern)(const C2<T>*, C2<T>*, long long, int, int, int, const T*, const C2<T>*) = nullptr;
+        switch (ilog2_c(L)) {
+            case 4: kern = fft_pow2_kernel<T, ADJ, 4>; break;
+            case 5: kern = fft_pow2_kernel<T, ADJ, 5>; break;
+            case 6: kern = fft_pow2_kernel<T, ADJ, 6>; break;
+            case 7: kern = fft_pow2_kernel<T, ADJ, 7>; break;
+            case 8: kern = fft_pow2_kernel<T, ADJ, 8>; break;
+            case 9: kern = fft_pow2_kernel<T, ADJ, 9>; break;
+            case 10: kern = fft_pow2_kernel<T, ADJ, 10>; break;
+            case 11: kern = fft_pow2_kernel<T, ADJ, 11>; break;
+            case 12: kern = fft_pow2_kernel<T, ADJ, 12>; break;
+            default: return fail(p, NFFTBL_EINTERNAL, "power-of-two FFT length out of range");
+        }
+        nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              static_cast<int>(smem)),
+                                      "fft smem attribute");
+        if (st != NFFTBL_OK) return st;
+        const int threads = std::max(64, std::min(kFftThreads, (W * L / 8 + 31) / 32 * 32));
+        timing_begin(p, NFFTBL_K_FFT);
+        kern<<<static_cast<unsigned>(blocks), threads, smem, p->stream>>>(src, dst, outer, static_cast<int>(inner), M,
+                                                                          ilog2_c(W), fac, tw);
+        timing_end(p);
+        p->launches++;
+        return check_cuda(p, cudaGetLastError(), "fft pass launch");
+    }
+    const int threads = fft_threads(L, W);
     auto kern = fft_pass_kernel<T, ADJ>;
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           static_cast<int>(smem)),
                                   "fft smem attribute");
     if (st != NFFTBL_OK) return st;
-    long long blocks = (inner == 1) ? (outer + W - 1) / W : outer * (inner / W);
     timing_begin(p, NFFTBL_K_FFT);
-    kern<<<static_cast<unsigned>(blocks), threads, smem, p->stream>>>(
-        static_cast<const C2<T>*>(in), static_cast<C2<T>*>(out), outer, static_cast<int>(inner), M, L, W,
-        static_cast<const T*>(p->facT[t].p), static_cast<const C2<T>*>(p->tw[t].p));
+    kern<<<static_cast<unsigned>(blocks), threads, smem, p->stream>>>(src, dst, outer, static_cast<int>(inner), M, L,
+                                                                      W, fac, tw);
     timing_end(p);
     p->launches++;
     return check_cuda(p, cudaGetLastError(), "fft pass launch");
