@@ -1421,7 +1421,7 @@ __global__ void __launch_bounds__(kTapThreads) spread1_kernel(const TapArgs<T> a
 
 // Ordered flush: grid[b][l] = sum over the boxes covering l, in a fixed order.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) gather_kernel(const TapArgs<T> a) {
+__global__ void __launch_bounds__(256, 8) gather_kernel(const TapArgs<T> a) {
     using CT = C2<T>;
     constexpr int kMaxCand = 48;   // >= 3 periodic images x (box/T + 1) tiles, T >= 2
     const long long total = static_cast<long long>(a.batch) * a.grid_stride;

@@ -408,3 +408,24 @@ def test_runtime_m_box_too_large_is_a_plan_error(prec, m):
     with pytest.raises(nb.NfftblError) as e:
         nb.Plan(3, 32, 2.0, m, precision=prec)
     assert e.value.name == "EUNSUPPORTED"
+
+
+def test_strided_fft_pass_covers_every_line():
+    """L = 90 (M = 60, sigma = 1.5) with a batch of 32: the pass over
+    dimension 0 has 32 x 90 strided lines, enough for several lines per
+    block; the lines per block must divide the inner extent 90 so that no
+    column is left out.  Grid, forward and adjoint against the oracle."""
+    batch = 32
+    plan = nb.Plan(2, 60, 1.5, 4, precision="f64", batch=batch)
+    assert tuple(plan.L) == (90, 90)
+    x = W.nodes_uniform(500, 2, dtype=np.float64, seed=8)
+    plan.set_nodes(to_dev(x))
+    op = oracle_plan(plan)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=np.complex128)
+    f = to_host(plan.forward(to_dev(fh)))
+    assert rel_l2(plan.grid(), O.grid_samples(op, fh)) < TOL["f64"]
+    assert rel_l2(f, O.forward(op, fh, x)) < TOL["f64"]
+    g = W.adjoint_input(500, batch=batch, dtype=np.complex128)
+    h = to_host(plan.adjoint(to_dev(g)))
+    plan.sync()
+    assert rel_l2(h, O.adjoint(op, g, x)) < TOL["f64"]
