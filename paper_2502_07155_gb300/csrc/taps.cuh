@@ -208,11 +208,12 @@ enum : int {
     WK_GENERIC = 0,     // any window / method: per-tap dispatch (out of line for cKB, table)
     WK_SINH = 1,        // Shannon method, sinh window
     WK_TABLE = 2,       // Shannon method, tabulated window (the learned phi_theta)
+    WK_CSINH = 3,       // classical method (Algorithm 2.1), sinh window
 };
 
 template <typename T>
 __device__ __forceinline__ int weight_kind(const WinParams<T>& w) {
-    if (w.method != NFFTBL_SHANNON) return WK_GENERIC;
+    if (w.method != NFFTBL_SHANNON) return (w.window == NFFTBL_WIN_SINH) ? WK_CSINH : WK_GENERIC;
     if (w.window == NFFTBL_WIN_SINH) return WK_SINH;
     if (w.window == NFFTBL_WIN_TABLE) return WK_TABLE;
     return WK_GENERIC;
@@ -250,9 +251,32 @@ __device__ __forceinline__ T shannon_table_weight(T tau, T s, int a, int m, cons
     return (u < T(1)) ? sc * ph : T(0);
 }
 
+// One classical-method tap weight (Algorithm 2.1) of the sinh window,
+// phi(delta) = sinh(beta sqrt(q)) / sinh(beta) with q = 1 - (delta/m)^2, zero
+// for |delta| >= m: the exponent pair of shannon_sinh_weight, one reciprocal,
+// no sinc factor.
+template <typename T>
+__device__ __forceinline__ T classic_sinh_weight(T tau, int a, int m, const WinParams<T>& wp) {
+    const int n = m - 1 - a;
+    const T delta = tau + static_cast<T>(n);
+    const T r = delta * wp.inv_m;
+    const T q = fma(-r, r, T(1));
+    const bool in = q > T(1e-30);
+    const T sq = FM<T>::sqrtw(in ? q : T(1));
+    const T one_sq = T(1) + sq;
+    const T rc = FM<T>::rcpw(one_sq);
+    const T e1 = FM<T>::exp2w(-wp.c_exp * (r * r) * rc);
+    const T e2 = FM<T>::exp2w(-wp.c_exp * one_sq);
+    return in ? (e1 - e2) * wp.c_norm : T(0);
+}
+
+// Tap weight a of the inline kind WK (not WK_GENERIC); s = sin(pi tau) is
+// used by the Shannon kinds only.
 template <typename T, int WK>
-__device__ __forceinline__ T shannon_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
-    return (WK == WK_TABLE) ? shannon_table_weight(tau, s, a, m, wp) : shannon_sinh_weight(tau, s, a, m, wp);
+__device__ __forceinline__ T fast_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
+    if constexpr (WK == WK_TABLE) return shannon_table_weight(tau, s, a, m, wp);
+    else if constexpr (WK == WK_CSINH) return classic_sinh_weight(tau, a, m, wp);
+    else return shannon_sinh_weight(tau, s, a, m, wp);
 }
 
 // The 2m tap weights psi_t(x - l/L) (Shannon) or phi_t(x - l/L) (classical)
@@ -267,7 +291,7 @@ __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w
         const T s = FM<T>::sinpi(tau);
 #pragma unroll
         for (int a = 0; a < TapN<W>::A; ++a)
-            if (a < nw) w[a] = shannon_weight<T, WK>(tau, s, a, m, wp);
+            if (a < nw) w[a] = fast_weight<T, WK>(tau, s, a, m, wp);
         return;
     }
     if (wp.method == NFFTBL_SHANNON) {
@@ -305,6 +329,9 @@ __device__ __forceinline__ void tap_weights_to(T* dst, int wk, T tau, const WinP
         const T s = FM<T>::sinpi(tau);
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) dst[a] = shannon_table_weight(tau, s, a, m, wp);
+    } else if (wk == WK_CSINH) {
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) dst[a] = classic_sinh_weight(tau, a, m, wp);
     } else {
         T wt[TapN<W>::A];
         tap_weights<T, W>(tau, wp, wt);
@@ -589,11 +616,12 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
     }
 }
 
-// Contraction of one batch entry for the Shannon / sinh or table plan (d >= 2) with
-// the dimension-0 weights evaluated inside the row loop: each is used once,
-// so they need no registers across the loop, and their SFU work overlaps
-// the rows' shared-memory loads and FMAs.  w1 (and w2) hold the other
-// dimensions' weights; s0 = sin(pi tau0).
+// Contraction of one batch entry for a plan with an inline weight kind WK
+// (Shannon sinh or table, classical sinh; d >= 2) with the dimension-0
+// weights evaluated inside the row loop: each is used once, so they need no
+// registers across the loop, and their SFU work overlaps the rows'
+// shared-memory loads and FMAs.  w1 (and w2) hold the other dimensions'
+// weights; s0 = sin(pi tau0) (unused by the classical kind).
 template <typename T, int D, int W, int WK>
 __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, const TileGeom& g, const int (&lb)[3],
                                                 T tau0, T s0, const T (&w1)[TapN<W>::A], const T (&w2)[TapN<W>::A],
@@ -606,7 +634,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         const C2<T>* p = box + lb[0] * pitch + lb[1];
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) {
-            const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
+            const T w0a = fast_weight<T, WK>(tau0, s0, a, m, wp);
             const C2<T>* row = p + a * pitch;
             C2<T> r = cmake<T>(T(0), T(0));
 #pragma unroll
@@ -619,7 +647,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
         const int p0 = g.box[1] * p1;
         const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
         for (int a = 0; a < nw; ++a) {
-            const T w0a = shannon_weight<T, WK>(tau0, s0, a, m, wp);
+            const T w0a = fast_weight<T, WK>(tau0, s0, a, m, wp);
             C2<T> mid = cmake<T>(T(0), T(0));
 #pragma unroll 2
             for (int b = 0; b < nw; ++b) {
@@ -679,9 +707,9 @@ __device__ __noinline__ void copy_factor_rows(const T* __restrict__ src, T* dst,
 }
 
 // One node of interp_kernel for every plan other than the single-batch
-// Shannon / sinh or table case (other windows, the classical method,
-// batches, compensated sums, stored factors): all weights in registers, then
-// one contraction per batch entry.  Kept out of line so that its registers do not count
+// case with an inline weight kind (the cKB window, d = 1, batches,
+// compensated sums, stored factors): all weights in registers, then one
+// contraction per batch entry.  Kept out of line so that its registers do not count
 // against the common path.
 template <typename T, int D, int W>
 __device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&lb)[3],
@@ -703,6 +731,10 @@ __device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T
         tap_weights<T, W, WK_TABLE>(tau[0], a.w, w0);
         if (D > 1) tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
         if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
+    } else if (wk == WK_CSINH) {
+        tap_weights<T, W, WK_CSINH>(tau[0], a.w, w0);
+        if (D > 1) tap_weights<T, W, WK_CSINH>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, WK_CSINH>(tau[2], a.w, w2);
     } else {
         tap_weights<T, W>(tau[0], a.w, w0);
         if (D > 1) tap_weights<T, W>(tau[1], a.w, w1);
@@ -801,6 +833,8 @@ __global__ void __launch_bounds__(256) factor_kernel(const TapArgs<T> a, T* __re
                 tap_weights<T, W, WK_SINH>(tau, a.w, w);
             else if (wk == WK_TABLE)
                 tap_weights<T, W, WK_TABLE>(tau, a.w, w);
+            else if (wk == WK_CSINH)
+                tap_weights<T, W, WK_CSINH>(tau, a.w, w);
             else
                 tap_weights<T, W>(tau, a.w, w);
 #pragma unroll
@@ -855,6 +889,14 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                     if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
                     a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_SINH>(
                         box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    continue;
+                }
+                if (!a.wfac && wk == WK_CSINH && D >= 2 && nb == 1 && a.comp == 0) {
+                    T w1[A], w2[A];
+                    tap_weights<T, W, WK_CSINH>(tau[1], a.w, w1);
+                    if (D > 2) tap_weights<T, W, WK_CSINH>(tau[2], a.w, w2);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_CSINH>(
+                        box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw);
                     continue;
                 }
                 if (!a.wfac && wk == WK_TABLE && D >= 2 && nb == 1 && a.comp == 0) {
