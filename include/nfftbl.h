@@ -176,7 +176,37 @@ nfftbl_status nfftbl_adjoint(nfftbl_plan_t plan, const void* f_dev, void* fhat_d
 nfftbl_status nfftbl_node_grad(nfftbl_plan_t plan, const void* fhat_dev, const void* gradf_dev,
                                void* gradx_dev);
 
-/* Wait for the plan's stream and report device-side failures of the work
+/*
+ * Forward and adjoint transforms with HOST input and output (same maps as
+ * nfftbl_forward / nfftbl_adjoint: Eq. 4.11 of Algorithm 4.2 and its
+ * transpose; Algorithm 2.1 for CLASSIC).
+ *   fhat_host : B x prod(M_t) complex, centred row-major (as fhat_dev);
+ *   f_host    : B x N complex in the caller's node order (as f_dev).
+ * The input is copied into a plan-owned device staging buffer on the plan's
+ * upload stream, the transform runs on the plan stream, and the output is
+ * copied back on the plan's download stream; events order each staging
+ * buffer between its copies and the transform that uses it, so consecutive
+ * calls overlap: the upload of an adjoint's input runs during the preceding
+ * forward transform, the download of a forward's output during the
+ * following adjoint.  Asynchronous: the outputs are in host memory after
+ * nfftbl_sync, or when work enqueued on the plan stream after nfftbl_join
+ * has completed.  The caller keeps the host buffers alive and unmodified
+ * (inputs) or unread (outputs) until then.  Page-locked host memory gives
+ * asynchronous copies; pageable memory works, with the copies staged
+ * synchronously by the CUDA runtime.  Errors as for nfftbl_forward, plus
+ * ENOMEM for the staging buffers (allocated on first use, kept until the
+ * plan is destroyed).
+ */
+nfftbl_status nfftbl_forward_host(nfftbl_plan_t plan, const void* fhat_host, void* f_host);
+nfftbl_status nfftbl_adjoint_host(nfftbl_plan_t plan, const void* f_host, void* fhat_host);
+
+/* Make later work on the plan stream wait for the downloads issued by the
+ * host-buffer calls so far (no host blocking).  Never fails for a valid plan
+ * whose CUDA context is healthy. */
+nfftbl_status nfftbl_join(nfftbl_plan_t plan);
+
+/* Wait for the plan's stream (and the upload and download streams of the
+ * host-buffer calls) and report device-side failures of the work
  * enqueued so far: ETIMEOUT if a bounded wait gave up (results invalid),
  * EINTERNAL for another device error word; the word is cleared. */
 nfftbl_status nfftbl_sync(nfftbl_plan_t plan);

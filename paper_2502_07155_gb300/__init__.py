@@ -38,6 +38,7 @@ EXPORTED = [
     "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
     "nfftbl_set_window_table", "nfftbl_window_loss_grad", "nfftbl_mlp_table", "nfftbl_mlp_backward",
     "nfftbl_mlp_param_count", "nfftbl_mlp_scratch_floats", "nfftbl_adam_step", "nfftbl_window_transform",
+    "nfftbl_forward_host", "nfftbl_adjoint_host", "nfftbl_join",
 ]
 KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin", "flush")
 
@@ -86,9 +87,11 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_set_stream.restype = st
     L.nfftbl_set_nodes.argtypes = [P, ctypes.c_int64, P]
     L.nfftbl_set_nodes.restype = st
-    for name in ("nfftbl_forward", "nfftbl_adjoint"):
+    for name in ("nfftbl_forward", "nfftbl_adjoint", "nfftbl_forward_host", "nfftbl_adjoint_host"):
         getattr(L, name).argtypes = [P, P, P]
         getattr(L, name).restype = st
+    L.nfftbl_join.argtypes = [P]
+    L.nfftbl_join.restype = st
     L.nfftbl_node_grad.argtypes = [P, P, P, P]
     L.nfftbl_node_grad.restype = st
     L.nfftbl_sync.argtypes = [P]
@@ -235,6 +238,30 @@ class Plan:
             raise ValueError(f"{name} must be contiguous")
         return ctypes.c_void_p(t.data_ptr())
 
+    def _host(self, t, shape, name):
+        """Data pointer of a contiguous host array of the plan's complex dtype:
+        a CPU torch tensor (page-locked for asynchronous copies) or a numpy
+        array."""
+        torch = _torch()
+        if isinstance(t, np.ndarray):
+            want = np.complex128 if self.precision == "f64" else np.complex64
+            if t.dtype != want:
+                raise TypeError(f"{name} must have dtype {np.dtype(want)}, got {t.dtype}")
+            if tuple(t.shape) != tuple(shape):
+                raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+            if not t.flags.c_contiguous:
+                raise ValueError(f"{name} must be C-contiguous")
+            return ctypes.c_void_p(t.ctypes.data)
+        if not isinstance(t, torch.Tensor) or t.is_cuda:
+            raise TypeError(f"{name} must be a CPU tensor or a numpy array")
+        if t.dtype != self._cdtype:
+            raise TypeError(f"{name} must have dtype {self._cdtype}, got {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+
     @property
     def handle(self):
         return self._h
@@ -271,6 +298,38 @@ class Plan:
         self._stream()
         self._check(self._lib.nfftbl_adjoint(self._h, pf, po))
         return out
+
+    def forward_host(self, fhat, out=None):
+        """forward() with host input and output (CPU tensors or numpy arrays;
+        page-locked tensors give asynchronous copies that overlap other calls'
+        transforms).  Asynchronous: the caller keeps fhat and out alive and
+        reads out after sync() (or after work on the plan stream that follows
+        join())."""
+        torch = _torch()
+        pi = self._host(fhat, (self.batch,) + self.M, "fhat")
+        if out is None:
+            out = torch.empty((self.batch, max(self.n_nodes, 0)), dtype=self._cdtype, pin_memory=True)
+        po = self._host(out, (self.batch, max(self.n_nodes, 0)), "out")
+        self._stream()
+        self._check(self._lib.nfftbl_forward_host(self._h, pi, po))
+        return out
+
+    def adjoint_host(self, f, out=None):
+        """adjoint() with host input and output; see forward_host."""
+        torch = _torch()
+        pi = self._host(f, (self.batch, max(self.n_nodes, 0)), "f")
+        if out is None:
+            out = torch.empty((self.batch,) + self.M, dtype=self._cdtype, pin_memory=True)
+        po = self._host(out, (self.batch,) + self.M, "out")
+        self._stream()
+        self._check(self._lib.nfftbl_adjoint_host(self._h, pi, po))
+        return out
+
+    def join(self):
+        """Order later work on the plan stream after the host-buffer calls'
+        downloads (no host blocking)."""
+        self._stream()
+        self._check(self._lib.nfftbl_join(self._h))
 
     def node_grad(self, fhat, grad_f, out=None):
         """grad_x[j, t] = sum_b Re(conj(grad_f[b, j]) d f_{b,j} / d x_{j,t}), shape (N, d)."""

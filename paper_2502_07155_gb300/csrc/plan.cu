@@ -265,6 +265,14 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->lw_dpsi);
     free_buf(p->err);
     if (p->err_host) cudaFreeHost(p->err_host);
+    free_buf(p->hs_fhat_in);
+    free_buf(p->hs_f_out);
+    free_buf(p->hs_f_in);
+    free_buf(p->hs_fhat_out);
+    for (auto& e : p->hev)
+        if (e) cudaEventDestroy(e);
+    if (p->s_up) cudaStreamDestroy(p->s_up);
+    if (p->s_down) cudaStreamDestroy(p->s_down);
     for (auto& t : p->timed) {
         if (t.a) cudaEventDestroy(t.a);
         if (t.b) cudaEventDestroy(t.b);
@@ -657,9 +665,106 @@ nfftbl_status nfftbl_spread_grid(nfftbl_plan_t p, const void* f_dev) {
     return taps(p, TAP_SPREAD, f_dev, nullptr, nullptr);
 }
 
+// ---- host-buffer entry points.  A transform's input is uploaded on the
+// plan's upload stream into a staging buffer and its output downloaded on the
+// download stream; events order each staging buffer between its copy and the
+// transform that uses it, so the upload of one call and the download of
+// another overlap the transforms on the plan stream.
+static nfftbl_status host_streams(nfftbl_plan_t p) {
+    nfftbl_status st = NFFTBL_OK;
+    if (!p->s_up) st = check_cuda(p, cudaStreamCreateWithFlags(&p->s_up, cudaStreamNonBlocking), "upload stream");
+    if (st == NFFTBL_OK && !p->s_down)
+        st = check_cuda(p, cudaStreamCreateWithFlags(&p->s_down, cudaStreamNonBlocking), "download stream");
+    for (int i = 0; st == NFFTBL_OK && i < nfftbl_plan_s::EV_COUNT; ++i)
+        if (!p->hev[i]) st = check_cuda(p, cudaEventCreateWithFlags(&p->hev[i], cudaEventDisableTiming), "event");
+    return st;
+}
+
+static nfftbl_status host_wait(nfftbl_plan_t p, cudaStream_t s, int ev) {
+    if (!p->hev_set[ev]) return NFFTBL_OK;
+    return check_cuda(p, cudaStreamWaitEvent(s, p->hev[ev], 0), "stream wait");
+}
+
+static nfftbl_status host_record(nfftbl_plan_t p, cudaStream_t s, int ev) {
+    p->hev_set[ev] = true;
+    return check_cuda(p, cudaEventRecord(p->hev[ev], s), "event record");
+}
+
+// One transform with host input and output: upload `in_bytes` from src into
+// stage_in (after the previous transform of this kind has read it), run
+// `run` on the plan stream into stage_out (after the previous download of
+// stage_out), download `out_bytes` into dst.
+extern "C++" {   // a template: C++ linkage inside the C-ABI block
+template <typename Run>
+static nfftbl_status host_transform(nfftbl_plan_t p, const void* src, size_t in_bytes, DeviceBuf& stage_in, void* dst,
+                                    size_t out_bytes, DeviceBuf& stage_out, int ev_in, int ev_done, int ev_out,
+                                    Run run) {
+    nfftbl_status st = host_streams(p);
+    if (st != NFFTBL_OK) return st;
+    const size_t cb = complex_bytes(p);
+    if ((st = ensure_buf(p, stage_in, std::max(in_bytes, cb))) != NFFTBL_OK) return st;
+    if ((st = ensure_buf(p, stage_out, std::max(out_bytes, cb))) != NFFTBL_OK) return st;
+    if (in_bytes > 0) {
+        if ((st = host_wait(p, p->s_up, ev_done)) != NFFTBL_OK) return st;
+        if ((st = check_cuda(p, cudaMemcpyAsync(stage_in.p, src, in_bytes, cudaMemcpyHostToDevice, p->s_up),
+                             "upload")) != NFFTBL_OK)
+            return st;
+        if ((st = host_record(p, p->s_up, ev_in)) != NFFTBL_OK) return st;
+        if ((st = host_wait(p, p->stream, ev_in)) != NFFTBL_OK) return st;
+    }
+    if ((st = host_wait(p, p->stream, ev_out)) != NFFTBL_OK) return st;
+    if ((st = run(stage_in.p, stage_out.p)) != NFFTBL_OK) return st;
+    if ((st = host_record(p, p->stream, ev_done)) != NFFTBL_OK) return st;
+    if (out_bytes > 0) {
+        if ((st = host_wait(p, p->s_down, ev_done)) != NFFTBL_OK) return st;
+        if ((st = check_cuda(p, cudaMemcpyAsync(dst, stage_out.p, out_bytes, cudaMemcpyDeviceToHost, p->s_down),
+                             "download")) != NFFTBL_OK)
+            return st;
+        if ((st = host_record(p, p->s_down, ev_out)) != NFFTBL_OK) return st;
+    }
+    return NFFTBL_OK;
+}
+}  // extern "C++"
+
+static size_t coeff_bytes(const nfftbl_plan_s* p) {
+    size_t n = static_cast<size_t>(p->batch) * complex_bytes(p);
+    for (int t = 0; t < p->d; ++t) n *= static_cast<size_t>(p->M[t]);
+    return n;
+}
+
+nfftbl_status nfftbl_forward_host(nfftbl_plan_t p, const void* fhat_host, void* f_host) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_host || (!f_host && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    const size_t out_bytes = static_cast<size_t>(p->batch) * static_cast<size_t>(p->N) * complex_bytes(p);
+    return host_transform(p, fhat_host, coeff_bytes(p), p->hs_fhat_in, f_host, out_bytes, p->hs_f_out,
+                          nfftbl_plan_s::EV_IN_FWD, nfftbl_plan_s::EV_FWD_DONE, nfftbl_plan_s::EV_OUT_F,
+                          [p](void* in, void* out) { return nfftbl_forward(p, in, out); });
+}
+
+nfftbl_status nfftbl_adjoint_host(nfftbl_plan_t p, const void* f_host, void* fhat_host) {
+    nfftbl_status st = ready(p);
+    if (st != NFFTBL_OK) return st;
+    if (!fhat_host || (!f_host && p->N > 0)) return fail(p, NFFTBL_EINVAL, "NULL data pointer");
+    const size_t in_bytes = static_cast<size_t>(p->batch) * static_cast<size_t>(p->N) * complex_bytes(p);
+    return host_transform(p, f_host, in_bytes, p->hs_f_in, fhat_host, coeff_bytes(p), p->hs_fhat_out,
+                          nfftbl_plan_s::EV_IN_ADJ, nfftbl_plan_s::EV_ADJ_DONE, nfftbl_plan_s::EV_OUT_FHAT,
+                          [p](void* in, void* out) { return nfftbl_adjoint(p, in, out); });
+}
+
+nfftbl_status nfftbl_join(nfftbl_plan_t p) {
+    if (!p) return NFFTBL_EINVAL;
+    nfftbl_status st = host_wait(p, p->stream, nfftbl_plan_s::EV_OUT_F);
+    if (st == NFFTBL_OK) st = host_wait(p, p->stream, nfftbl_plan_s::EV_OUT_FHAT);
+    return st;
+}
+
 nfftbl_status nfftbl_sync(nfftbl_plan_t p) {
     if (!p) return NFFTBL_EINVAL;
     nfftbl_status st;
+    if (p->s_up && (st = check_cuda(p, cudaStreamSynchronize(p->s_up), "upload stream sync")) != NFFTBL_OK) return st;
+    if (p->s_down && (st = check_cuda(p, cudaStreamSynchronize(p->s_down), "download stream sync")) != NFFTBL_OK)
+        return st;
     if ((st = check_cuda(p, cudaMemcpyAsync(p->err_host, p->err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream),
                          "read err")) != NFFTBL_OK)
         return st;
@@ -678,6 +783,8 @@ nfftbl_status nfftbl_destroy(nfftbl_plan_t p) {
     if (!p) return NFFTBL_OK;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
+    if (p->s_up) cudaStreamSynchronize(p->s_up);
+    if (p->s_down) cudaStreamSynchronize(p->s_down);
     destroy_plan(p);
     return NFFTBL_OK;
 }

@@ -229,6 +229,15 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf err;                // device error word
     int* err_host = nullptr;              // pinned mirror
 
+    // host-buffer entry points (nfftbl_forward_host / nfftbl_adjoint_host):
+    // staging buffers, an upload and a download stream, and the events that
+    // order each staging buffer's copies against the transform that uses it
+    nfftbl::DeviceBuf hs_fhat_in, hs_f_out, hs_f_in, hs_fhat_out;
+    cudaStream_t s_up = nullptr, s_down = nullptr;
+    enum { EV_IN_FWD, EV_IN_ADJ, EV_FWD_DONE, EV_ADJ_DONE, EV_OUT_F, EV_OUT_FHAT, EV_COUNT };
+    cudaEvent_t hev[EV_COUNT] = {};
+    bool hev_set[EV_COUNT] = {};
+
     // optional per-kernel timing (nfftbl_kernel_timing)
     bool timing = false;
     struct Timed {

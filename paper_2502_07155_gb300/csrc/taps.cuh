@@ -1293,7 +1293,6 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
                             int lb[3] = {0, 0, 0};
                             node_setup<T, 3>(a.xs, i, a.g, org, tau, lb, m);
                             T* row = s_tab + lane * RS;
-#pragma unroll
                             if (a.wfac) {   // stored factors (step 0b)
                                 copy_factor_rows<T, W>(a.wfac + i * a.wstride, row, 3, nw);
                             } else {
