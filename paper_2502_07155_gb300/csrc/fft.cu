@@ -11,9 +11,11 @@
 // Adjoint, t = 0, ..., d-1: load L_t values, forward-sign DFT, store only
 // k in I_{M_t} multiplied by (-1)^k d_t(k)  (F^H and D_psihat of Eq. 4.11).
 //
-// Each CTA transforms W lines of one pass in shared memory with a
-// mixed-radix (4, 2, 3, 5) Stockham autosort FFT; twiddles come from an FP64
-// table rounded to the plan's precision.
+// Each CTA transforms W lines of one pass in shared memory with a Stockham
+// autosort FFT: for L = 2^k a kernel instantiated per length with radix-8
+// stages (fft_pow2_kernel), otherwise run-time mixed radix (4, 2, 3, 5)
+// (fft_pass_kernel); twiddles come from an FP64 table rounded to the plan's
+// precision.
 #include <algorithm>
 
 #include "plan_internal.h"
