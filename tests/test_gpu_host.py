@@ -87,3 +87,28 @@ def test_host_calls_reject_device_tensors_and_bad_shapes():
         plan.forward_host(fh[:1])
     with pytest.raises(TypeError):
         plan.adjoint_host(np.zeros((2, N), dtype=np.complex128))
+
+
+def test_host_calls_without_nodes_and_with_growing_node_count():
+    """N = 0 (nothing to download for the forward, zeros from the adjoint),
+    then node sets of growing size: the staging buffers grow with N."""
+    plan = nb.Plan(2, 64, 2.0, 6, precision="f32")
+    plan.set_nodes(to_dev(np.zeros((0, 2), dtype=np.float32)))
+    fh = W.fhat_gaussian(plan.M, dtype=np.complex64)
+    f = plan.forward_host(torch.from_numpy(fh).pin_memory())
+    h = plan.adjoint_host(torch.zeros((1, 0), dtype=torch.complex64))
+    plan.sync()
+    assert tuple(f.shape) == (1, 0)
+    assert np.all(h.numpy() == 0)
+    for n in (100, 5000):
+        x = W.nodes_uniform(n, 2, seed=n)
+        plan.set_nodes(to_dev(x))
+        g = W.adjoint_input(n, dtype=np.complex64)
+        ref_f = to_host(plan.forward(to_dev(fh)))
+        ref_h = to_host(plan.adjoint(to_dev(g)))
+        plan.sync()
+        f = plan.forward_host(torch.from_numpy(fh).pin_memory())
+        h = plan.adjoint_host(torch.from_numpy(g).pin_memory())
+        plan.sync()
+        np.testing.assert_array_equal(f.numpy(), ref_f)
+        np.testing.assert_array_equal(h.numpy(), ref_h)
