@@ -580,6 +580,84 @@ def run_ours(args, cfg):
     return 0
 
 
+def run_ablation(args):
+    """Window, method, beta and precorrection ablations at d = 2, M = 256,
+    sigma = 2 on 2^20 held-out feasible nodes (Fourier data N(0,1) x
+    triangle): relative l2 error against the trigonometric sums (FP64
+    classical NFFT at m = 12) for m = 2..8, the FP32 forward time of each
+    configuration at the same size, and a sweep of beta around its default."""
+    import torch
+    from paper_2502_07155_gb300 import build
+    build.build()
+    import paper_2502_07155_gb300 as nb
+
+    d, M = 2, 256
+    L = 2 * M
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ms = list(range(2, 9))
+    x = W.nodes_feasible(1 << 20, d, max(ms) + 1, L, seed=W.SEED_HELDOUT)
+    fh = W.fhat_gaussian(M, d, seed=W.SEED_HELDOUT)
+    x64 = torch.from_numpy(x.astype(np.float64)).to(dev)
+    x32 = torch.from_numpy(x.astype(np.float32)).to(dev)
+    fh64 = torch.from_numpy(fh.astype(np.complex128)).to(dev)
+    fh32 = torch.from_numpy(fh.astype(np.complex64)).to(dev)
+    ref_plan = nb.Plan(d, M, 2.0, 12, precision="f64", method="classic")
+    ref_plan.set_nodes(x64)
+    ref = ref_plan.forward(fh64)
+    ref_plan.close()
+
+    def rel(a):
+        return float(torch.linalg.vector_norm(a.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref))
+
+    def error(m, precision="f64", **kw):
+        plan = nb.Plan(d, M, 2.0, m, precision=precision, **kw)
+        plan.set_nodes(x64 if precision == "f64" else x32)
+        e = rel(plan.forward(fh64 if precision == "f64" else fh32))
+        plan.close()
+        return e
+
+    def fwd_ms(m, **kw):
+        plan = nb.Plan(d, M, 2.0, m, precision="f32", **kw)
+        plan.set_nodes(x32)
+        out = torch.empty((1, x.shape[0]), dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            plan.forward(fh32, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            plan.forward(fh32, out=out)
+        b.record()
+        b.synchronize()
+        plan.close()
+        return a.elapsed_time(b) / 10
+
+    variants = {
+        "shannon_sinh": dict(method="shannon", window="sinh"),
+        "shannon_ckb": dict(method="shannon", window="ckb"),
+        "classic_sinh": dict(method="classic", window="sinh"),
+        "classic_ckb": dict(method="classic", window="ckb"),
+        "shannon_sinh_D=I": dict(method="shannon", window="sinh", precorrect=False),
+    }
+    table = {}
+    for name, kw in variants.items():
+        table[name] = {str(m): {"err_f64": error(m, **kw), "fwd_ms_f32": fwd_ms(m, **kw)} for m in ms}
+    for m in ms:
+        table["shannon_sinh"][str(m)]["err_f32"] = error(m, "f32", method="shannon", window="sinh")
+    sweep = {}
+    for m in (4, 6, 8):
+        b0 = nb.Plan(d, M, 2.0, m, precision="f64").beta
+        sweep[str(m)] = {f"{f:.2f}": error(m, method="shannon", window="sinh", beta=f * b0)
+                         for f in (0.6, 0.8, 0.9, 1.0, 1.1, 1.2, 1.4)}
+        sweep[str(m)]["beta_default"] = b0
+    print(json.dumps({"metric": "ablations: relative l2 error against the trigonometric sums, FP32 forward ms",
+                      "config": {"workload": "ablation_d2_M256_sigma2", "nodes": x.shape[0],
+                                 "nodes_kind": f"uniform feasible for m = {max(ms) + 1}",
+                                 "targets": "FP64 classical NFFT m=12"},
+                      "by_m": table, "beta_sweep": sweep}))
+    return 0
+
+
 def run_learned(args):
     """Learned window at d = 2, M = 256, sigma = 2: train phi_theta on 2^16
     feasible uniform nodes (Fourier data N(0,1) x triangle), then compare with
@@ -680,6 +758,8 @@ def main():
                     help="measure FP32 FMA and SFU lane rates per SM (roofline peaks)")
     ap.add_argument("--no-graph", action="store_true", dest="no_graph",
                     help="time stream-launched steps only (default: the headline replays the step as a CUDA graph)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="window / method / beta / precorrection ablations (d=2, M=256): error and FP32 forward time")
     ap.add_argument("--quick", action="store_true",
                     help="timed region only (no FP64, classical, end-to-end or oracle legs); for profiling")
     args = ap.parse_args()
@@ -693,6 +773,8 @@ def main():
         return run_reference(args, args.config)
     if args.learned:
         return run_learned(args)
+    if args.ablation:
+        return run_ablation(args)
     return run_ours(args, args.config)
 
 
