@@ -31,7 +31,7 @@ def nvcc() -> str:
     return path
 
 
-FIXED_M = (2, 3, 4, 5, 6, 8)      # must match NFFTBL_FIXED_M_LIST in plan_internal.h
+FIXED_M = (2, 3, 4, 5, 6, 7, 8)   # must match NFFTBL_FIXED_M_LIST in plan_internal.h
 GEN_DIR = os.path.join(OUT_DIR, "gen")
 
 

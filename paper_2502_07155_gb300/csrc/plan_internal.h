@@ -158,7 +158,7 @@ __host__ __forceinline__ size_t spread_min_smem(int d, int A, int box_cells, siz
 // takes m at run time.
 inline int tap_array_len(int m) {
     switch (m) {
-        case 2: case 3: case 4: case 5: case 6: case 8: return 2 * m;
+        case 2: case 3: case 4: case 5: case 6: case 7: case 8: return 2 * m;
         default: return 24;
     }
 }
@@ -302,6 +302,6 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
 template <typename T, int D>
 nfftbl_status run_taps_d(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem);
 // Compile-time tap counts W = 2m built by the generator (others use W = 0).
-#define NFFTBL_FIXED_M_LIST(X) X(2) X(3) X(4) X(5) X(6) X(8)
+#define NFFTBL_FIXED_M_LIST(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8)
 
 }  // namespace nfftbl

@@ -361,8 +361,9 @@ def test_adjoint_dense_cells(d, prec, method):
 
 # --------------------------------------------------------------------------- truncation m chosen at run time
 
-# Truncations outside the compile-time set {2, 3, 4, 5, 6, 8} run the kernels
-# that take m as an argument (tap arrays of length 24, loops bounded by 2m).
+# Truncations outside the compile-time set {2, ..., 8} (m = 9 .. 12) run the
+# kernels that take m as an argument (tap arrays of length 24, loops bounded
+# by 2m); the m = 7 cases run the compiled 2m = 14 kernels (odd m).
 RUNTIME_M = [
     (1, 256, 12, "f64", "shannon", "sinh", False),
     (1, 256, 9, "f32", "classic", "sinh", False),
