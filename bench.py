@@ -58,6 +58,9 @@ CONFIGS = {
     "d3_M128_m6_N2^20_spokes": (3, 128, 6, 1 << 20, 1, "spokes"),
 }
 DEFAULT_CONFIG = "d2_M256_m8_N2^20"
+# FP32 flavour of the timed plan: the d = 3 workload is specified with
+# compensated accumulation of the tap sums ("f32c"), the others plain FP32.
+PRECISION = {"d3_M128_m6_N2^23_spokes": "f32c", "d3_M128_m6_N2^20_spokes": "f32c"}
 
 # GB300 unit counts at the maximum SM clock (2070 MHz): 152 SMs; 128 FP32
 # FMA lanes per SM; the special-function unit issues 16 lanes per SM per clock
@@ -350,7 +353,7 @@ def run_ours(args, cfg):
     fh_d = torch.from_numpy(fh).to(dev)
     g_d = torch.from_numpy(g).to(dev)
 
-    plan = nb.Plan(d, M, 2.0, m, precision="f32", batch=B)
+    plan = nb.Plan(d, M, 2.0, m, precision=PRECISION.get(cfg, "f32"), batch=B)
     t0 = time.perf_counter()
     plan.set_nodes(x_d)
     t_set_first = time.perf_counter() - t0
@@ -476,6 +479,17 @@ def run_ours(args, cfg):
     cplan.sync()
     cplan.close()
 
+    # ---- FP32 with compensated (Neumaier) accumulation of the tap rows
+    kplan = nb.Plan(d, M, 2.0, m, precision="f32c", batch=B)
+    kplan.set_nodes(x_d)
+    for _ in range(2):
+        kplan.forward(fh_d, out=f_out)
+        kplan.adjoint(g_d, out=h_out)
+    comp_ms = timed(lambda: (kplan.forward(fh_d, out=f_out), kplan.adjoint(g_d, out=h_out)), 3)
+    f32c = kplan.forward(fh_d, out=f_out).clone()
+    kplan.sync()
+    kplan.close()
+
     # ---- plain FP64 GPU path on the same inputs
     plan64 = nb.Plan(d, M, 2.0, m, precision="f64", batch=B)
     x64 = torch.from_numpy(x.astype(np.float64)).to(dev)
@@ -492,6 +506,7 @@ def run_ours(args, cfg):
     f64 = plan64.forward(fh64, out=f64o)
     plan64.sync()
     err_fp32_fp64 = float(torch.linalg.vector_norm(f32.to(torch.complex128) - f64) / torch.linalg.vector_norm(f64))
+    err_fp32c_fp64 = float(torch.linalg.vector_norm(f32c.to(torch.complex128) - f64) / torch.linalg.vector_norm(f64))
     plan64.close()
 
     # ---- end to end through the C-ABI with pinned host buffers
@@ -550,7 +565,7 @@ def run_ours(args, cfg):
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg, "d": d, "M": M, "sigma": 2.0, "L": 2 * M, "m": m, "N": N, "batch": B,
-                       "nodes": kind, "window": "sinh", "beta": plan.beta,
+                       "nodes": kind, "window": "sinh", "beta": plan.beta, "precision": PRECISION.get(cfg, "f32"),
                        "step": "forward + adjoint (nodes binned once)", "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "launch": launch_mode, "stream_ms_per_step": t_stream},
@@ -569,6 +584,8 @@ def run_ours(args, cfg):
                                                          for k, v in ktimes.items()}},
             "fp64": {"ms_per_step": f64_ms, "nodes_per_s": N / (f64_ms * 1e-3), "speedup_fp32": f64_ms / t_step},
             "classic_nfft_fp32": {"ms_per_step": cls_ms, "nodes_per_s": N / (cls_ms * 1e-3)},
+            "fp32_compensated": {"ms_per_step": comp_ms, "nodes_per_s": N / (comp_ms * 1e-3),
+                                 "fp32c_vs_fp64_gpu_rel_l2": err_fp32c_fp64},
             "accuracy": {"fp32_vs_fp64_gpu_rel_l2": err_fp32_fp64,
                          **{k: v for k, v in cb.items() if k not in ("seconds", "n")}},
         }
