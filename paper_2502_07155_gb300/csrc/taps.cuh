@@ -621,14 +621,17 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
 // weights evaluated inside the row loop: each is used once, so they need no
 // registers across the loop, and their SFU work overlaps the rows'
 // shared-memory loads and FMAs.  w1 (and w2) hold the other dimensions'
-// weights; s0 = sin(pi tau0) (unused by the classical kind).
-template <typename T, int D, int W, int WK>
+// weights; s0 = sin(pi tau0) (unused by the classical kind).  COMP adds the
+// weighted row sums in compensated summation, as contract() does for the
+// compensated FP32 plans.
+template <typename T, int D, int W, int WK, bool COMP = false>
 __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, const TileGeom& g, const int (&lb)[3],
                                                 T tau0, T s0, const T (&w1)[TapN<W>::A], const T (&w2)[TapN<W>::A],
                                                 const WinParams<T>& wp, int nw_rt) {
     const int nw = W ? W : nw_rt;
     const int m = nw / 2;
     C2<T> acc = cmake<T>(T(0), T(0));
+    CompAcc<T> cacc;   // COMP: the weighted row sums in compensated (Neumaier) summation
     if (D == 2) {
         const int pitch = g.box[1];
         const C2<T>* p = box + lb[0] * pitch + lb[1];
@@ -640,7 +643,8 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
 #pragma unroll
             for (int b = 0; b < TapN<W>::A; ++b)
                 if (b < nw) r = cfma(row[b], w1[b], r);
-            acc = cfma(r, w0a, acc);
+            if constexpr (COMP) cacc.add(r.x * w0a, r.y * w0a);
+            else acc = cfma(r, w0a, acc);
         }
     } else {
         const int p1 = g.box[2];
@@ -656,11 +660,17 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
 #pragma unroll
                 for (int c = 0; c < TapN<W>::A; ++c)
                     if (c < nw) r = cfma(row[c], w2[c], r);
-                mid = cfma(r, w1[b], mid);
+                if constexpr (COMP) {
+                    const T wab = w0a * w1[b];
+                    cacc.add(r.x * wab, r.y * wab);
+                } else {
+                    mid = cfma(r, w1[b], mid);
+                }
             }
-            acc = cfma(mid, w0a, acc);
+            if constexpr (!COMP) acc = cfma(mid, w0a, acc);
         }
     }
+    if constexpr (COMP) return cmake<T>(cacc.sr + cacc.cr, cacc.si + cacc.ci);
     return acc;
 }
 
@@ -707,9 +717,9 @@ __device__ __noinline__ void copy_factor_rows(const T* __restrict__ src, T* dst,
 }
 
 // One node of interp_kernel for every plan other than the single-batch
-// case with an inline weight kind (the cKB window, d = 1, batches,
-// compensated sums, stored factors): all weights in registers, then one
-// contraction per batch entry.  Kept out of line so that its registers do not count
+// case with an inline weight kind (the cKB window, d = 1, batches, stored
+// factors): all weights in registers, then one contraction per batch
+// entry.  Kept out of line so that its registers do not count
 // against the common path.
 template <typename T, int D, int W>
 __device__ __noinline__ void interp_node_general(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&lb)[3],
@@ -883,28 +893,31 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 int lb[3] = {0, 0, 0};
                 node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
                 const long long dst = a.perm[i];
-                if (!a.wfac && wk == WK_SINH && D >= 2 && nb == 1 && a.comp == 0) {
+                if (!a.wfac && wk == WK_SINH && D >= 2 && nb == 1) {
                     T w1[A], w2[A];
                     tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_SINH>(
-                        box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] =
+                        a.comp ? contract_lazy0<T, D, W, WK_SINH, true>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw)
+                               : contract_lazy0<T, D, W, WK_SINH>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
                     continue;
                 }
-                if (!a.wfac && wk == WK_CSINH && D >= 2 && nb == 1 && a.comp == 0) {
+                if (!a.wfac && wk == WK_CSINH && D >= 2 && nb == 1) {
                     T w1[A], w2[A];
                     tap_weights<T, W, WK_CSINH>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_CSINH>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_CSINH>(
-                        box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] =
+                        a.comp ? contract_lazy0<T, D, W, WK_CSINH, true>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw)
+                               : contract_lazy0<T, D, W, WK_CSINH>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw);
                     continue;
                 }
-                if (!a.wfac && wk == WK_TABLE && D >= 2 && nb == 1 && a.comp == 0) {
+                if (!a.wfac && wk == WK_TABLE && D >= 2 && nb == 1) {
                     T w1[A], w2[A];
                     tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] = contract_lazy0<T, D, W, WK_TABLE>(
-                        box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                    a.fout[static_cast<long long>(b0) * a.N + dst] =
+                        a.comp ? contract_lazy0<T, D, W, WK_TABLE, true>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw)
+                               : contract_lazy0<T, D, W, WK_TABLE>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
                     continue;
                 }
                 interp_node_general<T, D, W>(a, box, slot, lb, tau, wk, b0, nb, i, dst);
