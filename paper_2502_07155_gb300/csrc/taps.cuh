@@ -177,14 +177,17 @@ template <int W> struct TapN {
 };
 
 // One Shannon / sinh tap weight (the FAST case of tap_weights) for tap a;
-// s = sin(pi tau).
+// sn = sin(pi tau) times the window's normalisation 1 / sinh(beta)
+// (sinh_sin() below; one product per node instead of one per weight).
 //
 // The exponent beta (sqrt(q) - 1) / ln 2 (up to 18 at m = 8) would multiply
 // the relative error of sqrt(q) by that much; it is evaluated as
-// -c r^2 / (1 + sqrt(q)) instead, where that error is damped.  One
-// reciprocal serves both 1/(1 + sqrt(q)) and the sinc's 1/(pi delta).
+// -c r^2 / (1 + sqrt(q)) instead, where that error is damped.  The two
+// reciprocals 1/(1 + sqrt(q)) and the sinc's 1/(pi delta) are separate SFU
+// operations: the kernels that use this routine are bound by instruction
+// issue, not by the SFU.
 template <typename T>
-__device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
+__device__ __forceinline__ T shannon_sinh_weight(T tau, T sn, int a, int m, const WinParams<T>& wp) {
     const int n = m - 1 - a;
     const T delta = tau + static_cast<T>(n);
     const T r = delta * wp.inv_m;
@@ -193,15 +196,14 @@ __device__ __forceinline__ T shannon_sinh_weight(T tau, T s, int a, int m, const
     const T sq = FM<T>::sqrtw(in ? q : T(1));
     const T one_sq = T(1) + sq;
     const bool centre = delta == T(0);
-    const T den = centre ? T(1) : static_cast<T>(kPiD) * delta;
-    const T rc = FM<T>::rcpw(den * one_sq);             // 1 / (pi delta (1 + sqrt q))
-    const T e1 = FM<T>::exp2w(-wp.c_exp * (r * r) * (rc * den));
+    const T inv1 = FM<T>::rcpw(one_sq);                  // 1 / (1 + sqrt q)
+    const T e1 = FM<T>::exp2w(-wp.c_exp * (r * r) * inv1);
     const T e2 = FM<T>::exp2w(-wp.c_exp * one_sq);
-    const T ph = (e1 - e2) * wp.c_norm;
-    const T num = (n & 1) ? -s : s;
-    const T sc = centre ? T(1) : num * (rc * one_sq);
-    return in ? sc * ph : T(0);
+    const T num = (n & 1) ? -sn : sn;
+    const T sc = centre ? wp.c_norm : num * FM<T>::rcpw(static_cast<T>(kPiD) * (centre ? T(1) : delta));
+    return in ? sc * (e1 - e2) : T(0);
 }
+
 
 // Weight kinds of the inline paths (chosen once per kernel from the plan).
 enum : int {
@@ -210,6 +212,14 @@ enum : int {
     WK_TABLE = 2,       // Shannon method, tabulated window (the learned phi_theta)
     WK_CSINH = 3,       // classical method (Algorithm 2.1), sinh window
 };
+
+// The sine factor the Shannon weights of kind WK take: sin(pi tau), times
+// the sinh window's normalisation for WK_SINH.
+template <typename T, int WK>
+__device__ __forceinline__ T kind_sin(T tau, const WinParams<T>& wp) {
+    const T s = FM<T>::sinpi(tau);
+    return (WK == WK_SINH) ? s * wp.c_norm : s;
+}
 
 template <typename T>
 __device__ __forceinline__ int weight_kind(const WinParams<T>& w) {
@@ -288,7 +298,7 @@ __device__ __forceinline__ void tap_weights(T tau, const WinParams<T>& wp, T (&w
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
     if (WK != WK_GENERIC) {
-        const T s = FM<T>::sinpi(tau);
+        const T s = kind_sin<T, WK>(tau, wp);
 #pragma unroll
         for (int a = 0; a < TapN<W>::A; ++a)
             if (a < nw) w[a] = fast_weight<T, WK>(tau, s, a, m, wp);
@@ -322,7 +332,7 @@ __device__ __forceinline__ void tap_weights_to(T* dst, int wk, T tau, const WinP
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
     if (wk == WK_SINH) {
-        const T s = FM<T>::sinpi(tau);
+        const T s = kind_sin<T, WK_SINH>(tau, wp);
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) dst[a] = shannon_sinh_weight(tau, s, a, m, wp);
     } else if (wk == WK_TABLE) {
@@ -350,7 +360,7 @@ __device__ __forceinline__ void tap_weights_to2(T* d0, T* d1, int wk, T tau0, T 
     }
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
-    const T s0 = FM<T>::sinpi(tau0), s1 = FM<T>::sinpi(tau1);
+    const T s0 = kind_sin<T, WK_SINH>(tau0, wp), s1 = kind_sin<T, WK_SINH>(tau1, wp);
 #pragma unroll 2
     for (int a = 0; a < nw; ++a) {
         d0[a] = shannon_sinh_weight(tau0, s0, a, m, wp);
@@ -621,7 +631,7 @@ __device__ __forceinline__ C2<T> contract(const C2<T>* __restrict__ box, const T
 // weights evaluated inside the row loop: each is used once, so they need no
 // registers across the loop, and their SFU work overlaps the rows'
 // shared-memory loads and FMAs.  w1 (and w2) hold the other dimensions'
-// weights; s0 = sin(pi tau0) (unused by the classical kind).  COMP adds the
+// weights; s0 = kind_sin<T, WK>(tau0) (unused by the classical kind).  COMP adds the
 // weighted row sums in compensated summation, as contract() does for the
 // compensated FP32 plans.
 template <typename T, int D, int W, int WK, bool COMP = false>
@@ -898,8 +908,10 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                     tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
                     if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
                     a.fout[static_cast<long long>(b0) * a.N + dst] =
-                        a.comp ? contract_lazy0<T, D, W, WK_SINH, true>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw)
-                               : contract_lazy0<T, D, W, WK_SINH>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
+                        a.comp ? contract_lazy0<T, D, W, WK_SINH, true>(box, a.g, lb, tau[0], kind_sin<T, WK_SINH>(tau[0], a.w),
+                                                                        w1, w2, a.w, nw)
+                               : contract_lazy0<T, D, W, WK_SINH>(box, a.g, lb, tau[0], kind_sin<T, WK_SINH>(tau[0], a.w),
+                                                                  w1, w2, a.w, nw);
                     continue;
                 }
                 if (!a.wfac && wk == WK_CSINH && D >= 2 && nb == 1) {
