@@ -78,8 +78,8 @@ SFU_SLOTS_PER_WEIGHT = 3.0
 # capture of the same workload and kernel version (the launch-list profile
 # summary of each workload); absent when not captured for the current code.
 NCU_TRAFFIC_BYTES = {
-    ("d2_M256_m8_N2^20", "spread"): 21122560,
-    ("d2_M256_m8_N2^20", "interp"): 14765568,
+    ("d2_M256_m8_N2^20", "spread"): 21113344,
+    ("d2_M256_m8_N2^20", "interp"): 14765824,
 }
 
 
