@@ -257,12 +257,6 @@ nfftbl_status nfftbl_get_grid(nfftbl_plan_t plan, void* host_out);
  * a caller may run step 3 (or its adjoint) on a grid it filled itself. */
 nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t plan, void** grid_dev);
 
-/*
- * Step 3 alone (Algorithm 4.2 step 3 / Algorithm 2.1 step 3): f = Psi grid
- * from the plan's current grid, and its transpose grid = Psi^T f (the grid is
- * cleared first).  For experiments that supply equispaced samples directly,
- * such as the exponential approximations of Eqs. 5.1-5.2.
- */
 /* The window transform at arbitrary real frequencies v (Eq. 4.2 for the
  * Shannon method: psi_hat(v) = int sinc(L pi x) phi(x) e^{-2 pi i v x} dx;
  * phi_hat(v) for CLASSIC), dimension t, in FP64 by the plan's own device
@@ -272,6 +266,12 @@ nfftbl_status nfftbl_grid_ptr(nfftbl_plan_t plan, void** grid_dev);
  * Asynchronous on the plan's stream.  Errors: EINVAL (t, n, NULL). */
 nfftbl_status nfftbl_window_transform(nfftbl_plan_t plan, int t, const double* v_dev, int n, double* out_dev);
 
+/*
+ * Step 3 alone (Algorithm 4.2 step 3 / Algorithm 2.1 step 3): f = Psi grid
+ * from the plan's current grid, and its transpose grid = Psi^T f (the grid is
+ * cleared first).  For experiments that supply equispaced samples directly,
+ * such as the exponential approximations of Eqs. 5.1-5.2.
+ */
 nfftbl_status nfftbl_interp_grid(nfftbl_plan_t plan, void* f_dev);
 nfftbl_status nfftbl_spread_grid(nfftbl_plan_t plan, const void* f_dev);
 
