@@ -430,3 +430,20 @@ def test_strided_fft_pass_covers_every_line():
     h = to_host(plan.adjoint(to_dev(g)))
     plan.sync()
     assert rel_l2(h, O.adjoint(op, g, x)) < TOL["f64"]
+
+
+@pytest.mark.parametrize("d,batch,prec", [(2, 8, "f32"), (2, 7, "f64"), (3, 5, "f32"), (3, 4, "f64")])
+def test_batch_larger_than_one_shared_memory_group(d, batch, prec):
+    """More batch entries than boxes fit in shared memory at once (6 at
+    d = 2, 3 at d = 3 for these shapes): the interpolation stages the tile's
+    boxes group by group with a ragged last group, the spreading groups its
+    boxes likewise.  Forward, adjoint and node gradient against the oracle."""
+    plan, x = make(d, prec, batch=batch)
+    op = oracle_plan(plan)
+    fh = W.fhat_gaussian(plan.M, batch=batch, dtype=CDT[prec], seed=21)
+    g = W.adjoint_input(x.shape[0], batch=batch, dtype=CDT[prec], seed=22)
+    assert rel_l2(to_host(plan.forward(to_dev(fh))), O.forward(op, fh, x)) < TOL[prec]
+    assert rel_l2(to_host(plan.adjoint(to_dev(g))), O.adjoint(op, g, x)) < TOL[prec]
+    gx = to_host(plan.node_grad(to_dev(fh), to_dev(g)))
+    plan.sync()
+    assert rel_l2(gx, O.node_grad(op, fh, x, g)) < (1e-10 if prec == "f64" else 1e-4)
