@@ -2,7 +2,8 @@
 (the transform does not shard on a one-GPU pool): the whole-job step time is
 the maximum over the ranks and the value counts the units of every rank.
 These tests run that host logic as two `gloo` ranks on CPU, and check that
-the reference arm leaves ranks other than 0 without work."""
+the reference arm leaves ranks other than 0 without work and prints the
+contract's line on rank 0."""
 import json
 import os
 import socket
