@@ -54,7 +54,7 @@ def test_no_gpu_calls_fail_cleanly_on_host(libpath):
     assert lib.nfftbl_plan(ctypes.byref(h), 1, M1, 2.0, 6, 0, None) == 1         # odd M
     assert lib.nfftbl_plan(ctypes.byref(h), 1, M, 2.0, 300, 0, None) == 1        # 2m >= L
     M3 = (ctypes.c_int * 3)(100, 0, 0)
-    assert lib.nfftbl_plan(ctypes.byref(h), 1, M3, 1.1, 4, 0, None) == 3         # L = 110 not 2^p
+    assert lib.nfftbl_plan(ctypes.byref(h), 1, M3, 1.1, 4, 0, None) == 3         # L = 110 = 2 5 11: not 2^a 3^b 5^c
     assert lib.nfftbl_plan(ctypes.byref(h), 1, M, 2.0, 13, 0, None) == 3         # m > 12
     assert lib.nfftbl_plan(None, 1, M, 2.0, 6, 0, None) == 1
     assert lib.nfftbl_destroy(None) == 0
