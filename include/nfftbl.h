@@ -238,6 +238,9 @@ typedef struct {
     int key_bits;           /* bits of the binning key                               */
 } nfftbl_info;
 
+/* The plan's parameters (after defaults: L_t, beta, tile extents) and, once
+ * nodes are set, the binning sizes, into caller-owned host memory.  Errors:
+ * EINVAL (NULL plan or info). */
 nfftbl_status nfftbl_get_info(nfftbl_plan_t plan, nfftbl_info* info);
 
 /* Precorrection factors of dimension t: d_t(k) = 1/(L_t psi_hat_t(k)),

@@ -4,12 +4,14 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2502_07155_gb300 as nb
 from paper_2502_07155_gb300 import build as nbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nfftbl.h")
 
 
 def declared_functions():
@@ -61,3 +63,29 @@ def test_no_gpu_calls_fail_cleanly_on_host(libpath):
     assert lib.nfftbl_set_nodes(None, 0, None) == 1
     assert lib.nfftbl_forward(None, None, None) == 1
     assert lib.nfftbl_last_error(None) == b"NULL plan"
+
+
+def test_every_declaration_is_documented():
+    """Each C-ABI declaration (or a group of adjacent ones) sits directly under
+    a comment that states its meaning, layout, ownership and errors."""
+    lines = open(HEADER).read().split("\n")
+    undocumented = []
+    for i, line in enumerate(lines):
+        if re.match(r"^(nfftbl_status|const char\*|int64_t|int|size_t|void)\s+nfftbl_\w+\(", line):
+            j = i - 1
+            while j >= 0 and re.match(r"^(nfftbl_status|const char\*|int64_t|int|size_t|void)\s+nfftbl_\w+\(", lines[j]):
+                j -= 1   # a group of declarations shares the comment above it
+            while j >= 0 and lines[j].startswith(" ") and not lines[j].strip().endswith("*/"):
+                j -= 1   # continuation lines of a multi-line declaration
+            if j < 0 or not lines[j].rstrip().endswith("*/"):
+                undocumented.append(line[:60])
+    assert not undocumented, undocumented
+
+
+def test_fig_5_1_frequency_grid():
+    """v_s = -M/2 - m + s/S for s = 0 .. S (M + 2m) (Fig. 5.1)."""
+    from paper_2502_07155_gb300.experiments import fig51_frequencies
+    v = fig51_frequencies(20, 5, 32)
+    assert v.size == 32 * 30 + 1
+    assert v[0] == -15.0 and v[-1] == 15.0
+    np.testing.assert_allclose(np.diff(v), 1 / 32, rtol=0, atol=1e-15)
