@@ -25,7 +25,7 @@ __all__ = [
     "oversampled_length", "default_beta", "Window", "Plan", "make_plan",
     "sinc", "dsinc", "window_transform", "precorrection_factors",
     "fourier_matrix", "step1_precorrect", "mlp_backward", "learned_table_grad", "window_loss", "step2_idft", "step3_short_sums",
-    "forward", "grid_samples", "adjoint", "adjoint_short_sums",
+    "forward", "grid_samples", "adjoint", "adjoint_short_sums", "adjoint_short_sums_at",
     "adjoint_idft", "ndft", "ndft_adjoint", "node_derivative", "node_grad",
     "bin_nodes", "tap_ranges", "dense_matrices", "mlp_init", "mlp_forward",
     "learned_table", "catmull_rom",
@@ -446,6 +446,35 @@ def adjoint_short_sums(plan: Plan, g: np.ndarray, x: np.ndarray) -> np.ndarray:
             u[bi] += np.bincount(flat, weights=contrib.real, minlength=size)
             u[bi] += 1j * np.bincount(flat, weights=contrib.imag, minlength=size)
     return u.reshape((B,) + tuple(plan.L))
+
+
+def adjoint_short_sums_at(plan: Plan, g: np.ndarray, x: np.ndarray, cells) -> np.ndarray:
+    """u_l = sum_j g_j psi(x_j - l/L) (Psi^T g, the transpose of the short
+    sums of Eq. 4.8) at the listed grid points only, straight from the
+    definition: for every listed l (storage indices, shape (n_cells, d)) and
+    every node, the product of the d one-dimensional kernels at
+    x_{j,t} - l_t/L_t, taken where |L_t x_{j,t} - l_t| <= m in every
+    dimension.  For Algorithm 2.1 the index difference is reduced modulo L_t
+    to its nearest image (periodized window).  Returns shape (B, n_cells).
+
+    Equal to adjoint_short_sums at those points; it needs only the nodes
+    whose taps reach them, so large node sets can be checked on a few cells."""
+    g = np.asarray(g, dtype=np.complex128)
+    x = np.asarray(x, dtype=np.float64)
+    cells = np.asarray(cells, dtype=np.int64).reshape(-1, plan.d)
+    out = np.zeros((g.shape[0], cells.shape[0]), dtype=np.complex128)
+    for c, cell in enumerate(cells):
+        w = np.ones(x.shape[0], dtype=np.float64)
+        for t in range(plan.d):
+            L = plan.L[t]
+            ell = int(cell[t]) - L // 2                   # l_t in I_L
+            delta = L * x[:, t] - ell                     # L x - l, exact for L = 2^p
+            if plan.method == "classic":
+                delta = delta - L * np.round(delta / L)
+            inside = np.abs(delta) <= plan.m
+            w = w * np.where(inside, plan.kernel(t, delta / L), 0.0)
+        out[:, c] = g @ w
+    return out
 
 
 def adjoint_idft(plan: Plan, u: np.ndarray) -> np.ndarray:

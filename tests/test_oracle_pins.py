@@ -311,6 +311,26 @@ def test_dense_matrix_form(d, method):
     np.testing.assert_allclose(O.adjoint(p, g, x, fac).reshape(-1), A.conj().T @ g[0], rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("d,method", [(1, "shannon"), (2, "shannon"), (3, "shannon"),
+                                      (1, "classic"), (2, "classic"), (3, "classic")])
+def test_adjoint_short_sums_at_points(d, method):
+    """Psi^T g evaluated straight from its definition at selected grid points
+    equals the scattered (bincount) form at those points, including points
+    on the grid's edges (zero extension, resp. the periodic wrap of
+    Algorithm 2.1) and nodes on both domain edges."""
+    M = {1: 32, 2: 16, 3: 8}[d]
+    p = O.make_plan(d, M, 2.0, 3, method=method)
+    x = W.nodes_uniform(400, d, dtype=np.float64, seed=15)
+    x = np.concatenate([x, np.full((2, d), -0.5), np.full((2, d), np.nextafter(0.5, 0.0))])
+    g = W.adjoint_input(x.shape[0], batch=2, dtype=np.complex128)
+    full = O.adjoint_short_sums(p, g, x).reshape(2, -1)
+    rng = np.random.default_rng(3)
+    cells = rng.integers(0, p.L[0], size=(40, d))
+    cells = np.concatenate([cells, np.zeros((1, d), np.int64), np.full((1, d), p.L[0] - 1)])
+    flat = np.ravel_multi_index(tuple(cells.T), p.L)
+    np.testing.assert_allclose(O.adjoint_short_sums_at(p, g, x, cells), full[:, flat], rtol=1e-13, atol=1e-14)
+
+
 def test_ndft_adjoint_is_transpose():
     x = W.nodes_uniform(40, 2, dtype=np.float64)
     fh = W.fhat_gaussian(8, 2, dtype=np.complex128)
