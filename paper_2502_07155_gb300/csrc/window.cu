@@ -204,6 +204,21 @@ cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m
     return cudaGetLastError();
 }
 
+cudaError_t upload_gl_rule_sync() {
+    static GLRule rule;
+    cudaError_t e = cudaMemcpyToSymbol(c_gl_x, rule.x, sizeof(rule.x), 0, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gl_w, rule.w, sizeof(rule.w), 0, cudaMemcpyHostToDevice);
+    return e;
+}
+
+cudaError_t launch_window_factors_preloaded(int with_sinc, int window, int L, int M, int m, double beta,
+                                            double* fac64_out, cudaStream_t s) {
+    const int panels = (window == NFFTBL_WIN_TABLE) ? kTablePanels : 96;
+    window_factor_kernel<<<M, 256, 0, s>>>(with_sinc, window, L, M, m, beta, nullptr, 0, panels, nullptr,
+                                           fac64_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_window_transform(int with_sinc, int window, int L, int m, double beta, const double* table,
                                     int table_n, const double* v, int n, double* out, cudaStream_t s) {
     static GLRule rule;
