@@ -211,6 +211,21 @@ nfftbl_status nfftbl_join(nfftbl_plan_t plan);
  * EINTERNAL for another device error word; the word is cleared. */
 nfftbl_status nfftbl_sync(nfftbl_plan_t plan);
 
+/* Limit of the plan's bounded device-side waits (the interpolation and
+ * node-derivative kernels' waits for a TMA tile copy), in nanoseconds of the
+ * GPU's global timer: limit_ns in [1, 6e10]; 0 restores the default of 2 s.
+ * A wait that runs out abandons the transform (its outputs are invalid),
+ * lets its copy in flight land, sets the plan's device error word and
+ * returns, so that the CUDA context stays usable; the next nfftbl_sync
+ * reports ETIMEOUT and clears the word.
+ * stall_next != 0 arms a test of that path: in the next interpolation
+ * launch the tile waits are armed but no copy is issued, so nothing can
+ * complete them and every wait runs out after limit_ns (a failure made on
+ * purpose, without faulting the device).  Not in the paper: a safety
+ * device of this implementation.  Errors: EINVAL (NULL plan, limit out of
+ * range). */
+nfftbl_status nfftbl_set_wait_limit(nfftbl_plan_t plan, int64_t limit_ns, int stall_next);
+
 /* Release the plan and all of its device memory.  NULL is accepted.  The
  * handle must not be used again. */
 nfftbl_status nfftbl_destroy(nfftbl_plan_t plan);
@@ -366,21 +381,23 @@ nfftbl_status nfftbl_adam_step(float* params_dev, const float* grad_dev, float* 
  *
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc: code running under another framework's memory
- * pool or allocator hooks, code that must not allocate while a CUDA graph is
- * being captured, or hosts that only hand out buffers they allocated
- * themselves.  nfftbl_plan allocates (window factors, grid, scratch), so such
- * callers cannot use a plan; this call needs none.
+ * pool or allocator hooks (where a library's own device allocations are not
+ * allowed or not visible to the owner of the memory), or hosts that only hand
+ * out buffers they allocated themselves.  nfftbl_plan allocates (window
+ * factors, grid, scratch), so such callers cannot use a plan; this call needs
+ * none.
  *
  * It computes what nfftbl_forward computes before its short sums: the
- * precorrected, zero-padded, oversampled inverse FFT of fhat (steps 1-2,
- * vartheta of Eq. 4.7) for the Shannon method with the sinh window, in FP32:
+ * precorrected, zero-padded, oversampled inverse FFT of fhat, i.e. the
+ * equispaced samples the short sums read, for the Shannon method with the
+ * sinh window, in FP32:
  *   d, M, sigma, m, beta, batch : as for nfftbl_plan (beta <= 0: default
  *                                 pi m (1 - 1/sigma)); batch B >= 1;
  *   fhat_dev  : B x prod(M_t) complex64 input (centred, row-major), caller-owned;
  *   grid_dev  : B x prod(L_t) complex64 output (centred, row-major), caller-owned;
  *   cuda_stream : cudaStream_t the work is enqueued on (NULL = legacy stream).
  * The result equals the grid a plan with the same parameters holds after
- * nfftbl_forward.
+ * nfftbl_forward.  L_t = 2^a 3^b 5^c in [16, 4096], as for nfftbl_plan.
  *
  * It allocates nothing: the window factors, twiddles and intermediate FFT
  * passes live in one fixed device array of 16 MiB inside the library, which
@@ -388,11 +405,18 @@ nfftbl_status nfftbl_adam_step(float* params_dev, const float* grad_dev, float* 
  * whose factors, twiddles and intermediates need more than 16 MiB
  * (d = 2: about B * M_0 * L_1 * 8 bytes; d = 3: B * M_0 * L_2 * (M_1 + L_1) * 8
  * bytes) are rejected with NFFTBL_EINVAL and a message naming the size.
- * The first call on a device looks up that device's address of the array
- * (with the device current); make the first call on each device before any
- * stream capture.  Every call shares the one array and leaves its contents
- * behind: calls whose work overlaps on the GPU (different streams, or
- * different threads without ordering) race on it, so serialise them.
+ * The first call on a device sets that device up, with the device current:
+ * it looks up the device's address of the array and copies the quadrature
+ * rule of the window factors to the device (a synchronous copy); make the
+ * first call on each device before any stream capture.  Later calls only
+ * launch kernels.  A call whose parameters (d, M, L, m, beta) equal the
+ * previous call's on the same device reuses the window factors that call
+ * left in the array instead of repeating their quadrature.
+ * Every call shares the one array and leaves its contents behind: calls
+ * whose work overlaps on the GPU (different streams, or different threads
+ * without ordering) race on it, so serialise them.  The device address is
+ * looked up once per process and device: calls after cudaDeviceReset (or any
+ * other re-creation of the device's primary context) are not supported.
  * Asynchronous; errors: EINVAL, EUNSUPPORTED (as for nfftbl_plan), ECUDA.
  * The message of a failed call is available from nfftbl_plan_error().
  */
