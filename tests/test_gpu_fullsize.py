@@ -1,9 +1,12 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
-uses, on outputs the oracle can compute one by one (sampled nodes), plus
-properties that hold at any size (the adjoint identity, finite values).
+uses, on outputs the oracle can compute one by one (sampled nodes, selected
+grid cells), element by element over the whole grid where the oracle
+finishes in seconds, plus properties that hold at any size (the adjoint
+identity, finite values).
 
-Workloads: d=2 M=256 N=2^20 (m = 4, 6, 8; both methods), d=3 M=128 N=2^23
-radial spokes (m = 6), d=2 M=512 N=4e6 batch 8 (m = 6) with gradients.
+Workloads: d=2 M=256 N=2^20 (m = 4, 6, 8; both methods; FP32 and FP64),
+d=3 M=128 N=2^23 radial spokes (m = 6 and 8; FP32 and FP64), d=2 M=512
+N=4e6 batch 8 (m = 6) with gradients.
 """
 import numpy as np
 import pytest
@@ -115,7 +118,7 @@ def test_d2_M512_N4e6_B8_gradients():
             vals = O.nfft_oracle._gather_tensor(grid[b], [p[0] for p in per])
             der[b, :, t] = np.sum(vals * wt, axis=(1, 2))
     ref_gx = np.sum(np.real(np.conj(gf_np[:, idx])[:, :, None] * der), axis=0)
-    assert rel_l2(gx, ref_gx) < 1e-4
+    assert rel_l2(gx, ref_gx) < 1e-5
     # central differences (h = 1e-4 / L in FP64, one Richardson step) on the oracle's map
     v = W.fd_directions(idx.size, d)
 
@@ -129,3 +132,106 @@ def test_d2_M512_N4e6_B8_gradients():
     lhs = torch.vdot(to_dev(gf_np).reshape(-1).to(torch.complex128), f.detach().reshape(-1).to(torch.complex128))
     rhs = torch.vdot(fh.grad.reshape(-1).to(torch.complex128), fh.detach().reshape(-1).to(torch.complex128))
     assert float(abs(lhs - rhs) / abs(lhs)) < 1e-5
+
+
+# --------------------------------------------------------------------------- element-wise adjoint at full size
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f32c": 1e-5}
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_d2_M256_N2e20_adjoint_elementwise(prec):
+    """The whole transposed short-sum grid Psi^T g (512^2 cells) and the
+    whole adjoint D F^H Psi^T g (256^2 coefficients) of all 2^20 nodes at
+    m = 8, element by element against the oracle."""
+    d, M, m, N = 2, 256, 8, 1 << 20
+    rdt, cdt = (np.float64, np.complex128) if prec == "f64" else (np.float32, np.complex64)
+    plan = nb.Plan(d, M, 2.0, m, precision=prec)
+    x = W.nodes_uniform(N, d, dtype=rdt)
+    g = W.adjoint_input(N, dtype=cdt)
+    plan.set_nodes(to_dev(x))
+    h = to_host(plan.adjoint(to_dev(g)))
+    plan.spread_grid(to_dev(g))
+    u = plan.grid()
+    op = oracle_plan(plan)
+    u_ref = O.adjoint_short_sums(op, g, x)
+    assert rel_l2(u, u_ref) < TOL[prec]
+    fac = O.precorrection_factors(op)
+    h_ref = O.adjoint_idft(op, u_ref) * fac[0][None, :, None] * fac[1][None, None, :]
+    assert rel_l2(h, h_ref) < TOL[prec]
+
+
+def test_d2_M256_N2e20_f64_forward_sampled():
+    """FP64 forward of all 2^20 nodes at m = 8, sampled nodes against the
+    oracle at the FP64 tolerance."""
+    d, M, m, N = 2, 256, 8, 1 << 20
+    plan = nb.Plan(d, M, 2.0, m, precision="f64")
+    x = W.nodes_uniform(N, d, dtype=np.float64)
+    fh = W.fhat_gaussian(M, d, dtype=np.complex128)
+    plan.set_nodes(to_dev(x))
+    f = to_host(plan.forward(to_dev(fh)))
+    idx = sample_idx(N)
+    assert rel_l2(f[:, idx], O.forward(oracle_plan(plan), fh, x[idx])) < TOL["f64"]
+
+
+def spoke_cell_blocks(L, m, T=8):
+    """Grid cells (storage indices) for the spoke workload: the 2x2x2 cells
+    at the centre where every spoke meets (the densest cells), 2x2x2 cells
+    straddling tile boundaries in the sparse part (several boxes of the
+    ordered flush cover them), the grid's first and last cells (zero
+    extension at the edge of I_L) and a few single cells."""
+    h = L // 2
+    blocks = [
+        [(h - 1 + a, h - 1 + b, h - 1 + c) for a in (0, 1) for b in (0, 1) for c in (0, 1)],
+        [(3 * T - 1 + a, 5 * T - 1 + b, 2 * T - 1 + c) for a in (0, 1) for b in (0, 1) for c in (0, 1)],
+        [(L - 4 * T - 1 + a, h + T - 1 + b, L - 2 * T - 1 + c) for a in (0, 1) for b in (0, 1) for c in (0, 1)],
+        [(0, 0, 0), (L - 1, L - 1, L - 1), (1, h, L - 2)],
+        [(h + 40, h - 30, h + 5), (h - 7, h + 9, h + 2)],
+    ]
+    return [np.array(b, dtype=np.int64) for b in blocks]
+
+
+def nodes_reaching(x, cells, L, m):
+    """Indices of the nodes whose taps can reach any of the cells."""
+    lo = cells.min(axis=0) - L // 2 - m - 1
+    hi = cells.max(axis=0) - L // 2 + m + 1
+    u = L * x.astype(np.float64)
+    return np.flatnonzero(np.all((u >= lo) & (u <= hi), axis=1))
+
+
+@pytest.mark.parametrize("m,prec", [(6, "f32c"), (8, "f32c"), (6, "f64")])
+def test_d3_M128_N2e23_spread_cells(m, prec):
+    """Transposed short sums of all 2^23 spoke nodes (no re-binning: the
+    full-density runs, long same-cell runs at the centre, many items per
+    tile) at selected cells against the oracle's definition evaluated from
+    the nodes that reach them; then the sampled forward."""
+    d, M = 3, 128
+    rdt, cdt = (np.float64, np.complex128) if prec == "f64" else (np.float32, np.complex64)
+    plan = nb.Plan(d, M, 2.0, m, precision=prec)
+    x = W.nodes_spokes().astype(rdt)
+    N = x.shape[0]
+    g = W.adjoint_input(N, dtype=cdt)
+    plan.set_nodes(to_dev(x))
+    _, _, off = plan.binning()
+    assert np.diff(off.astype(np.int64)).max() > 4 * 1024     # the centre tiles hold several work items
+    plan.spread_grid(to_dev(g))
+    grid = plan.grid_tensor()
+    op = oracle_plan(plan)
+    L = plan.L[0]
+    got_all, ref_all = [], []
+    for cells in spoke_cell_blocks(L, m):
+        sel = nodes_reaching(x, cells, L, m)
+        ref = O.adjoint_short_sums_at(op, g[:, sel], x[sel], cells)
+        idx = torch.from_numpy(cells).cuda()
+        got = to_host(grid[0, idx[:, 0], idx[:, 1], idx[:, 2]])[None, :]
+        if np.linalg.norm(ref) > 0:
+            assert rel_l2(got, ref) < TOL[prec], (cells[0], sel.size)
+        else:
+            assert np.all(got == 0)
+        got_all.append(got)
+        ref_all.append(ref)
+    assert rel_l2(np.concatenate(got_all, axis=1), np.concatenate(ref_all, axis=1)) < TOL[prec]
+    fh = W.fhat_gaussian(M, d, dtype=cdt)
+    f = to_host(plan.forward(to_dev(fh)))
+    idx = np.unique(np.concatenate([sample_idx(N, 1500), np.argsort(np.abs(x).max(axis=1))[:300]]))
+    assert rel_l2(f[:, idx], O.forward(op, fh, x[idx])) < TOL[prec]
