@@ -38,7 +38,7 @@ EXPORTED = [
     "nfftbl_kernel_timing", "nfftbl_kernel_times", "nfftbl_grid_noalloc",
     "nfftbl_set_window_table", "nfftbl_window_loss_grad", "nfftbl_mlp_table", "nfftbl_mlp_backward",
     "nfftbl_mlp_param_count", "nfftbl_mlp_scratch_floats", "nfftbl_adam_step", "nfftbl_window_transform",
-    "nfftbl_forward_host", "nfftbl_adjoint_host", "nfftbl_join",
+    "nfftbl_forward_host", "nfftbl_adjoint_host", "nfftbl_join", "nfftbl_set_wait_limit",
 ]
 KERNEL_CLASSES = ("fft", "interp", "spread", "grad", "bin", "flush")
 
@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
     L.nfftbl_join.restype = st
     L.nfftbl_node_grad.argtypes = [P, P, P, P]
     L.nfftbl_node_grad.restype = st
+    L.nfftbl_set_wait_limit.argtypes = [P, ctypes.c_int64, ctypes.c_int]
+    L.nfftbl_set_wait_limit.restype = st
     L.nfftbl_sync.argtypes = [P]
     L.nfftbl_sync.restype = st
     L.nfftbl_destroy.argtypes = [P]
@@ -385,6 +387,12 @@ class Plan:
 
     def sync(self):
         self._check(self._lib.nfftbl_sync(self._h))
+
+    def set_wait_limit(self, limit_ns: int = 0, stall_next: bool = False):
+        """Limit of the bounded tile-copy waits in ns (0: the default 2 s);
+        stall_next arms the next interpolation's waits with nothing to
+        complete them (a test of the timeout path)."""
+        self._check(self._lib.nfftbl_set_wait_limit(self._h, int(limit_ns), 1 if stall_next else 0))
 
     def info(self) -> dict:
         inf = _Info()

@@ -237,6 +237,110 @@ __global__ void emit_work_kernel(const uint32_t* __restrict__ off, const uint32_
     }
 }
 
+// Same-cell pairs for the interpolation: one warp per work item walks the
+// item's sorted keys 32 at a time.  Node j at position r of its run of equal
+// keys (nodes of one cell) is a pair head when r is even; its partner is
+// node j + 1 when that node is in the same run and in the same item.  The
+// heads of an item are written in order to heads[start ..), each as the
+// node's sorted index with bit 31 set when it has a partner; nheads[item]
+// counts them.  Every node is a head or the partner of the head before it.
+__global__ void pair_heads_kernel(const uint32_t* __restrict__ keys, const WorkItem* __restrict__ work, int n_work,
+                                  uint32_t* __restrict__ heads, uint32_t* __restrict__ nheads) {
+    const unsigned full = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < n_work; item += gridDim.x * wpb) {
+        const WorkItem wi = work[item];
+        uint32_t prev_key = 0xFFFFFFFFu;   // keys are < 2^31: differs from every key
+        int prev_pos = -1;
+        int out = 0;
+        for (int base = 0; base < wi.count; base += 32) {
+            const int j = base + lane;
+            const bool valid = j < wi.count;
+            const uint32_t key = valid ? keys[wi.start + j] : 0xFFFFFFFEu;
+            uint32_t up = __shfl_up_sync(full, key, 1);
+            if (lane == 0) up = prev_key;
+            const bool start = valid && key != up;
+            const unsigned sb = __ballot_sync(full, start);
+            const unsigned le = sb & ((lane == 31) ? full : ((2u << lane) - 1u));
+            const int pos = le ? lane - (31 - __clz(static_cast<int>(le))) : prev_pos + 1 + lane;
+            uint32_t dn = __shfl_down_sync(full, key, 1);
+            if (lane == 31) dn = (j + 1 < wi.count) ? keys[wi.start + j + 1] : 0xFFFFFFFDu;
+            const bool head = valid && (pos & 1) == 0;
+            const bool paired = head && j + 1 < wi.count && dn == key;
+            const unsigned hb = __ballot_sync(full, head);
+            if (head)
+                heads[wi.start + out + __popc(hb & ((1u << lane) - 1u))] =
+                    static_cast<uint32_t>(wi.start + j) | (paired ? 0x80000000u : 0u);
+            out += __popc(hb);
+            prev_key = __shfl_sync(full, key, 31);
+            prev_pos = __shfl_sync(full, pos, 31);
+        }
+        if (lane == 0) nheads[item] = static_cast<uint32_t>(out);
+    }
+}
+
+// Order of the pair heads inside each d = 3 work item, against shared-memory
+// bank conflicts of the interpolation: the 8-byte box value a head loads at
+// tap (a, b, c) lies in bank pair (base + a p0 + b p1 + c) mod 16, base =
+// lb0 p0 + lb1 p1 + lb2 the offset of its first tap, and the tap offsets are
+// the same for every thread.  Heads of different base classes (mod 16) never
+// conflict.  The heads are dealt class by class: all first heads of each
+// class in class order, then all second heads, ..., so that consecutive
+// heads (one per thread of a half warp) have distinct classes as far as the
+// item's classes allow.  One warp per item; counts per class in shared
+// memory.
+__global__ void order_heads_kernel(const uint32_t* __restrict__ keys, const WorkItem* __restrict__ work, int n_work,
+                                   const uint32_t* __restrict__ in_heads, const uint32_t* __restrict__ nheads,
+                                   TileGeom g, int m, uint32_t* __restrict__ out_heads) {
+    constexpr int kWarps = 8;
+    __shared__ uint32_t cnt[kWarps][16], run[kWarps][16];
+    const unsigned full = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p1 = g.box[2], p0 = g.box[1] * p1;
+    auto cls_of = [&](uint32_t key) {
+        const int lin = static_cast<int>(key & ((1u << g.cells_per_tile_log2) - 1u));
+        const int l2 = lin % g.T[2], l1 = (lin / g.T[2]) % g.T[1], l0 = lin / (g.T[2] * g.T[1]);
+        const int base = (l0 + g.off[0] - (m - 1)) * p0 + (l1 + g.off[1] - (m - 1)) * p1 + (l2 + g.off[2] - (m - 1));
+        return base & 15;
+    };
+    for (int item = blockIdx.x * kWarps + w; item < n_work; item += gridDim.x * kWarps) {
+        const WorkItem wi = work[item];
+        const int nh = static_cast<int>(nheads[item]);
+        if (lane < 16) {
+            cnt[w][lane] = 0;
+            run[w][lane] = 0;
+        }
+        __syncwarp();
+        for (int base = 0; base < nh; base += 32) {
+            const int h = base + lane;
+            if (h < nh) atomicAdd(&cnt[w][cls_of(keys[in_heads[wi.start + h] & 0x7FFFFFFFu])], 1u);
+        }
+        __syncwarp();
+        for (int base = 0; base < nh; base += 32) {
+            const int h = base + lane;
+            const bool valid = h < nh;
+            const uint32_t hv = valid ? in_heads[wi.start + h] : 0u;
+            const int cls = valid ? cls_of(keys[hv & 0x7FFFFFFFu]) : 16 + lane;   // (unique when invalid)
+            const unsigned peers = __match_any_sync(full, cls);
+            const unsigned before = peers & ((1u << lane) - 1u);
+            if (valid) {
+                const uint32_t r = run[w][cls] + __popc(before);
+                uint32_t pos = 0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const uint32_t n = cnt[w][c];
+                    pos += min(n, r) + ((c < cls && n > r) ? 1u : 0u);
+                }
+                out_heads[wi.start + pos] = hv;
+            }
+            __syncwarp();
+            if (valid && before == 0) run[w][cls] += __popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
 inline unsigned grid1d(long long n, int threads) {
     return static_cast<unsigned>((n + threads - 1) / threads);
 }
@@ -355,6 +459,33 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
         NFFTBL_OK) {
         p->N = -1;
         return st;
+    }
+    // same-cell pairs of the interpolation (heads per item)
+    if ((st = ensure_buf(p, p->heads, Nb * 4)) != NFFTBL_OK || (st = ensure_buf(p, p->nheads,
+                                                                                std::max<uint32_t>(host_total, 1) * 4)) != NFFTBL_OK) {
+        p->N = -1;
+        return st;
+    }
+    if (host_total > 0) {
+        const unsigned blocks = static_cast<unsigned>(std::min<long long>((host_total + 7) / 8, 8LL * p->num_sms));
+        // d = 3: heads in sorted order into the (now free) sort scratch, then dealt by bank class
+        const bool deal = d == 3;
+        uint32_t* first = deal ? static_cast<uint32_t*>(p->keys_tmp.p) : static_cast<uint32_t*>(p->heads.p);
+        pair_heads_kernel<<<blocks, 256, 0, s>>>(kA, static_cast<const WorkItem*>(p->work.p),
+                                                 static_cast<int>(host_total), first,
+                                                 static_cast<uint32_t*>(p->nheads.p));
+        p->launches++;
+        if (deal) {
+            order_heads_kernel<<<blocks, 256, 0, s>>>(kA, static_cast<const WorkItem*>(p->work.p),
+                                                      static_cast<int>(host_total), first,
+                                                      static_cast<const uint32_t*>(p->nheads.p), p->geom, p->m,
+                                                      static_cast<uint32_t*>(p->heads.p));
+            p->launches++;
+        }
+        if ((st = check_cuda(p, cudaGetLastError(), "pair heads launch")) != NFFTBL_OK) {
+            p->N = -1;
+            return st;
+        }
     }
     p->n_work = host_total;
     p->N = N;

@@ -148,11 +148,15 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
     a.xs = static_cast<const T*>(p->xs.p);
     a.perm = static_cast<const uint32_t*>(p->perm.p);
     a.work = static_cast<const WorkItem*>(p->work.p);
+    a.heads = static_cast<const uint32_t*>(p->heads.p);
+    a.nheads = static_cast<const uint32_t*>(p->nheads.p);
     a.n_work = static_cast<int>(p->n_work);
     a.N = p->N;
     a.grid = static_cast<C2<T>*>(p->grid.p);
     a.grid_stride = prod_L(p);
     a.err = static_cast<int*>(p->err.p);
+    a.wait_ns = p->wait_ns;
+    a.stall = 0;
     a.part = static_cast<C2<T>*>(p->part.p);
     a.tile_items = static_cast<const uint32_t*>(p->tile_items.p);
     a.wbound = T(1);
@@ -209,10 +213,16 @@ nfftbl_status run_taps(nfftbl_plan_s* p, int kind, const void* fin, void* fout, 
     a.fin = static_cast<const C2<T>*>(fin);
     a.fout = static_cast<C2<T>*>(fout);
     a.gradx = static_cast<T*>(gradx);
+    if (kind == TAP_INTERP && p->stall_next) {   // one launch only
+        a.stall = 1;
+        p->stall_next = 0;
+    }
     // box slots padded to 128 bytes, plus 128 bytes to align the base
     const size_t slot = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
     size_t smem = static_cast<size_t>(a.batch_smem) * slot + 128;
-    if (kind == TAP_SPREAD) {
+    if (kind == TAP_SPREAD && spread3c_applies(p->d, sizeof(T) == 4, p->m, p->geom.T)) {
+        smem = spread3c_smem(p->m);   // (the launcher sets it again with the kernel)
+    } else if (kind == TAP_SPREAD) {
         int nb = 1, sub = 32;
         if (!spread_config<T>(p, nb, sub, smem))
             return fail(p, NFFTBL_EUNSUPPORTED, "spread box does not fit in shared memory");
@@ -258,6 +268,8 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->work);
     free_buf(p->tile_items);
     free_buf(p->part);
+    free_buf(p->heads);
+    free_buf(p->nheads);
     free_buf(p->counters);
     free_buf(p->lw_f);
     free_buf(p->lw_h);
@@ -446,8 +458,9 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
         const bool tma_ok = 2 * g.box[d - 1] <= 256 && (d < 2 || g.box[0] <= 256) && (d < 3 || g.box[1] <= 256);
         const int bc = static_cast<int>(box_cells(g));
         const int A = tap_array_len(m);
-        const size_t spread_min = (o.precision == NFFTBL_F64) ? spread_min_smem<double>(d, A, bc, optin)
-                                                              : spread_min_smem<float>(d, A, bc, optin);
+        size_t spread_min = (o.precision == NFFTBL_F64) ? spread_min_smem<double>(d, A, bc, optin)
+                                                        : spread_min_smem<float>(d, A, bc, optin);
+        if (spread3c_applies(d, o.precision != NFFTBL_F64, m, T)) spread_min = spread3c_smem(m);
         if (bytes <= kBoxMax && tma_ok && spread_min <= static_cast<size_t>(optin)) break;
         if (user_tile) return plan_fail(nullptr, NFFTBL_EUNSUPPORTED, "tile box exceeds shared memory or TMA limits");
         int big = 0;
@@ -776,6 +789,14 @@ nfftbl_status nfftbl_sync(nfftbl_plan_t p) {
         if (e & DEVERR_TIMEOUT) return fail(p, NFFTBL_ETIMEOUT, "a bounded device wait gave up");
         return fail(p, NFFTBL_EINTERNAL, "device error word set");
     }
+    return NFFTBL_OK;
+}
+
+nfftbl_status nfftbl_set_wait_limit(nfftbl_plan_t p, int64_t limit_ns, int stall_next) {
+    if (!p) return NFFTBL_EINVAL;
+    if (limit_ns < 0 || limit_ns > 60000000000LL) return fail(p, NFFTBL_EINVAL, "limit_ns must be in [0, 6e10]");
+    p->wait_ns = limit_ns ? static_cast<unsigned long long>(limit_ns) : kWaitLimitNs;
+    p->stall_next = stall_next ? 1 : 0;
     return NFFTBL_OK;
 }
 

@@ -50,6 +50,8 @@ struct TapArgs {
     const uint32_t* perm;      // sorted -> caller index
     const WorkItem* work;
     int n_work;
+    const uint32_t* heads;     // pair heads of each item (sorted index | partner flag << 31), or null
+    const uint32_t* nheads;    // heads per item
     long long N;
     C2<T>* grid;               // B x prod(L)
     long long grid_stride;     // prod(L)
@@ -57,6 +59,8 @@ struct TapArgs {
     C2<T>* fout;               // B x N (interp output)
     T* gradx;                  // N x d (node gradient output)
     int* err;
+    unsigned long long wait_ns;   // limit of the box-staging waits (nfftbl_set_wait_limit)
+    int stall;                 // 1: the staging waits are armed but nothing completes them (timeout test)
     // spreading
     C2<T>* part;               // n_work x B x box cells: per-item boxes (ordered flush)
     const uint32_t* tile_items;// n_tiles + 1: first work item of each tile
@@ -145,6 +149,56 @@ __host__ __forceinline__ int spread3_warps(int A, int box_cells, size_t limit) {
     return 8;
 }
 
+// Column-owner d = 3 spreading (FP32, tiles of 8 x 8 x 8 cells, compile-time
+// W = 2m, 4 <= W <= 16): every lane of the block owns one column
+// (c1, c2) of the item's box and keeps the box's R cells along dimension 0
+// of that column in registers; warps own patches of 4 x 8 columns.  The
+// node table holds, per node, its window values of each dimension placed at
+// their box positions (zero elsewhere: R rows for dimension 0, 4 P1 and 8 P2
+// columns for dimensions 1 and 2), its input value and the mask of the warps
+// whose patch meets its window.  Two tables of C nodes (one third of the
+// block's threads: one thread per node and dimension fills them) alternate.
+template <int W>
+struct Spread3C {
+    static constexpr int T = 8;                       // tile extent, every dimension
+    static constexpr int R = T + W - 1;               // box extent, dimension 0 (rows)
+    static constexpr int RP = (R + 3) / 4 * 4;        // rows padded to whole float4s
+    static constexpr int B1 = T + W - 1;              // box extent, dimension 1
+    static constexpr int B2 = T + W;                  // box extent, dimension 2 (even origin)
+    static constexpr int P1 = (B1 + 3) / 4;           // warp patches along dimension 1 (4 columns)
+    static constexpr int P2 = (B2 + 7) / 8;           // and along dimension 2 (8 columns)
+    static constexpr int WARPS = P1 * P2;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int C = THREADS / 3;             // nodes per table
+    static constexpr int O1 = RP;                     // dimension-1 values (4 P1 entries)
+    static constexpr int O2 = RP + 4 * P1;            // dimension-2 values (8 P2 entries)
+    static constexpr int OM = O2 + 8 * P2;            // g.x, g.y, warp mask, unused
+    static constexpr int ROW = OM + 4;                // node-table row, floats (16-byte multiple)
+    static constexpr size_t SMEM = 2 * static_cast<size_t>(C) * ROW * sizeof(float);
+    static_assert(WARPS <= 32, "warp mask is 32 bits");
+};
+
+// Shared memory of the column-owner d = 3 spreading kernel for truncation m
+// (0 if it does not exist for m).
+inline size_t spread3c_smem(int m) {
+    switch (m) {
+        case 2: return Spread3C<4>::SMEM;
+        case 3: return Spread3C<6>::SMEM;
+        case 4: return Spread3C<8>::SMEM;
+        case 5: return Spread3C<10>::SMEM;
+        case 6: return Spread3C<12>::SMEM;
+        case 7: return Spread3C<14>::SMEM;
+        case 8: return Spread3C<16>::SMEM;
+        default: return 0;
+    }
+}
+
+// Whether an FP32 d = 3 plan spreads with the column-owner kernel: a
+// compile-time truncation and 8 x 8 x 8 tiles.
+inline bool spread3c_applies(int d, bool fp32, int m, const int* T) {
+    return d == 3 && fp32 && m >= 2 && m <= 8 && T[0] == 8 && T[1] == 8 && T[2] == 8;
+}
+
 // Shared memory of the spread kernel for dimension d (minimum batch group).
 template <typename T>
 __host__ __forceinline__ size_t spread_min_smem(int d, int A, int box_cells, size_t limit) {
@@ -220,6 +274,7 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf work;               // WorkItem list
     nfftbl::DeviceBuf tile_items;         // n_tiles + 1: first work item per tile
     nfftbl::DeviceBuf part;               // spread boxes, one slot per (item, batch entry)
+    nfftbl::DeviceBuf heads, nheads;      // same-cell pair heads per work item (interpolation)
     nfftbl::DeviceBuf counters;           // small device scratch (ints)
     long long n_tiles = 0;
     long long n_work = 0;
@@ -228,6 +283,8 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf lw_f, lw_h, lw_marg, lw_dpsi;   // learned-window loss/gradient scratch
     nfftbl::DeviceBuf err;                // device error word
     int* err_host = nullptr;              // pinned mirror
+    unsigned long long wait_ns = nfftbl::kWaitLimitNs;   // limit of the box-staging waits
+    int stall_next = 0;                   // next interpolation: waits that nothing completes (timeout test)
 
     // host-buffer entry points (nfftbl_forward_host / nfftbl_adjoint_host):
     // staging buffers, an upload and a download stream, and the events that
@@ -267,6 +324,12 @@ nfftbl_status check_cuda(nfftbl_plan_s* p, cudaError_t e, const char* what);
 cudaError_t launch_window_factors(int with_sinc, int window, int L, int M, int m, double beta,
                                   const double* table, int table_n, double* fac64_out,
                                   cudaStream_t s);
+// The quadrature rule the window-factor kernels read, copied to the current
+// device once and synchronously; launch_window_factors_preloaded then
+// launches the kernel alone (no copy), for a closed-form window (no table).
+cudaError_t upload_gl_rule_sync();
+cudaError_t launch_window_factors_preloaded(int with_sinc, int window, int L, int M, int m, double beta,
+                                            double* fac64_out, cudaStream_t s);
 cudaError_t launch_cast_factors(const double* fac64, int M, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_twiddles(int L, void* out, int is_double, cudaStream_t s);
 cudaError_t launch_window_transform(int with_sinc, int window, int L, int m, double beta, const double* table,

@@ -684,6 +684,139 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
     return acc;
 }
 
+// contract_lazy0 for two nodes of one cell (same first taps lb): every box
+// value is loaded once and enters both nodes' sums, which halves the
+// shared-memory traffic of the pair.  Node b's arithmetic is node a's with
+// its own weights, so each result equals contract_lazy0 of that node alone.
+template <typename T, int D, int W, int WK, bool COMP = false>
+__device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ box, const TileGeom& g,
+                                                    const int (&lb)[3], T tau0a, T s0a, const T (&w1a)[TapN<W>::A],
+                                                    const T (&w2a)[TapN<W>::A], T tau0b, T s0b,
+                                                    const T (&w1b)[TapN<W>::A], const T (&w2b)[TapN<W>::A],
+                                                    const WinParams<T>& wp, int nw_rt, C2<T>& outa, C2<T>& outb) {
+    const int nw = W ? W : nw_rt;
+    const int m = nw / 2;
+    C2<T> acca = cmake<T>(T(0), T(0)), accb = cmake<T>(T(0), T(0));
+    CompAcc<T> ca, cb;
+    if constexpr (D == 2) {
+        const int pitch = g.box[1];
+        const C2<T>* p = box + lb[0] * pitch + lb[1];
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) {
+            const T w0a = fast_weight<T, WK>(tau0a, s0a, a, m, wp);
+            const T w0b = fast_weight<T, WK>(tau0b, s0b, a, m, wp);
+            const C2<T>* row = p + a * pitch;
+            C2<T> ra = cmake<T>(T(0), T(0)), rb = cmake<T>(T(0), T(0));
+#pragma unroll
+            for (int b = 0; b < TapN<W>::A; ++b) {
+                if (b < nw) {
+                    const C2<T> v = row[b];
+                    ra = cfma(v, w1a[b], ra);
+                    rb = cfma(v, w1b[b], rb);
+                }
+            }
+            if constexpr (COMP) {
+                ca.add(ra.x * w0a, ra.y * w0a);
+                cb.add(rb.x * w0b, rb.y * w0b);
+            } else {
+                acca = cfma(ra, w0a, acca);
+                accb = cfma(rb, w0b, accb);
+            }
+        }
+    } else if constexpr (D == 3) {
+        const int p1 = g.box[2];
+        const int p0 = g.box[1] * p1;
+        const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
+        for (int a = 0; a < nw; ++a) {
+            const T w0a = fast_weight<T, WK>(tau0a, s0a, a, m, wp);
+            const T w0b = fast_weight<T, WK>(tau0b, s0b, a, m, wp);
+            C2<T> mida = cmake<T>(T(0), T(0)), midb = cmake<T>(T(0), T(0));
+#pragma unroll 2
+            for (int b = 0; b < nw; ++b) {
+                const C2<T>* row = p + a * p0 + b * p1;
+                C2<T> ra = cmake<T>(T(0), T(0)), rb = cmake<T>(T(0), T(0));
+#pragma unroll
+                for (int c = 0; c < TapN<W>::A; ++c) {
+                    if (c < nw) {
+                        const C2<T> v = row[c];
+                        ra = cfma(v, w2a[c], ra);
+                        rb = cfma(v, w2b[c], rb);
+                    }
+                }
+                if constexpr (COMP) {
+                    const T wa = w0a * w1a[b], wb = w0b * w1b[b];
+                    ca.add(ra.x * wa, ra.y * wa);
+                    cb.add(rb.x * wb, rb.y * wb);
+                } else {
+                    mida = cfma(ra, w1a[b], mida);
+                    midb = cfma(rb, w1b[b], midb);
+                }
+            }
+            if constexpr (!COMP) {
+                acca = cfma(mida, w0a, acca);
+                accb = cfma(midb, w0b, accb);
+            }
+        }
+    }
+    if constexpr (COMP) {
+        outa = cmake<T>(ca.sr + ca.cr, ca.si + ca.ci);
+        outb = cmake<T>(cb.sr + cb.cr, cb.si + cb.ci);
+    } else {
+        outa = acca;
+        outb = accb;
+    }
+}
+
+// The inline-weight interpolation of a pair head: nodes ia and ib (= ia
+// when the head has no partner) of one cell, weights of dimensions 1 .. d-1
+// in registers, dimension-0 weights evaluated per row.
+template <typename T, int D, int W, int WK>
+__device__ __forceinline__ void interp_pair(const TapArgs<T>& a, const C2<T>* box, const int (&lb)[3],
+                                            const T (&taua)[3], const T (&taub)[3], int nw, C2<T>& fa, C2<T>& fb) {
+    constexpr int A = TapN<W>::A;
+    T w1a[A], w2a[A], w1b[A], w2b[A];
+    tap_weights<T, W, WK>(taua[1], a.w, w1a);
+    tap_weights<T, W, WK>(taub[1], a.w, w1b);
+    if constexpr (D > 2) {
+        tap_weights<T, W, WK>(taua[2], a.w, w2a);
+        tap_weights<T, W, WK>(taub[2], a.w, w2b);
+    }
+    const T s0a = (WK == WK_CSINH) ? T(0) : (WK == WK_SINH) ? kind_sin<T, WK_SINH>(taua[0], a.w) : FM<T>::sinpi(taua[0]);
+    const T s0b = (WK == WK_CSINH) ? T(0) : (WK == WK_SINH) ? kind_sin<T, WK_SINH>(taub[0], a.w) : FM<T>::sinpi(taub[0]);
+    if (a.comp)
+        contract_lazy0_pair<T, D, W, WK, true>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w, nw,
+                                               fa, fb);
+    else
+        contract_lazy0_pair<T, D, W, WK>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w, nw, fa, fb);
+}
+
+// The inline-weight interpolation of one node (FP64 plans): weights of
+// dimensions 1 .. d-1 in registers, dimension-0 weights evaluated per row.
+template <typename T, int D, int W>
+__device__ __forceinline__ C2<T> interp_single(const TapArgs<T>& a, const C2<T>* box, const int (&lb)[3],
+                                               const T (&tau)[3], int wk, int nw) {
+    constexpr int A = TapN<W>::A;
+    T w1[A], w2[A];
+    if (wk == WK_SINH) {
+        tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
+        const T s0 = kind_sin<T, WK_SINH>(tau[0], a.w);
+        return a.comp ? contract_lazy0<T, D, W, WK_SINH, true>(box, a.g, lb, tau[0], s0, w1, w2, a.w, nw)
+                      : contract_lazy0<T, D, W, WK_SINH>(box, a.g, lb, tau[0], s0, w1, w2, a.w, nw);
+    }
+    if (wk == WK_CSINH) {
+        tap_weights<T, W, WK_CSINH>(tau[1], a.w, w1);
+        if (D > 2) tap_weights<T, W, WK_CSINH>(tau[2], a.w, w2);
+        return a.comp ? contract_lazy0<T, D, W, WK_CSINH, true>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw)
+                      : contract_lazy0<T, D, W, WK_CSINH>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw);
+    }
+    tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
+    if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
+    const T s0 = FM<T>::sinpi(tau[0]);
+    return a.comp ? contract_lazy0<T, D, W, WK_TABLE, true>(box, a.g, lb, tau[0], s0, w1, w2, a.w, nw)
+                  : contract_lazy0<T, D, W, WK_TABLE>(box, a.g, lb, tau[0], s0, w1, w2, a.w, nw);
+}
+
 // Copy n = 2m (n <= A) window factors from src to dst with the widest
 // aligned vector accesses the compile-time tap count allows (the stored
 // rows and their per-dimension parts start 16-byte aligned when 2m is a
@@ -791,7 +924,7 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap* tmap, const TapArgs
                                           int slot, const int (&org)[3], bool wrap, int b0, int nb, uint64_t* bar,
                                           uint32_t& phase) {
     if (!wrap) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !a.stall) {   // (stall: nothing arrives, the wait must run out)
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, static_cast<uint32_t>(nb * box_cells * sizeof(C2<T>)));
             for (int bb = 0; bb < nb; ++bb) {
@@ -804,7 +937,7 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap* tmap, const TapArgs
                     tma_load_4d(dst, tmap, 2 * org[2], org[1], org[0], b0 + bb, bar);
             }
         }
-        const bool ok = mbar_wait_bounded(bar, phase, a.err);
+        const bool ok = mbar_wait_bounded(bar, phase, a.err, a.wait_ns);
         phase ^= 1u;
         return __syncthreads_and(ok) != 0;   // one verdict for the whole block
     }
@@ -884,7 +1017,6 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
     uint32_t phase = 0;
     const bool periodic = a.w.method == NFFTBL_CLASSIC;
     const int wk = weight_kind(a.w);
-    constexpr int A = TapN<W>::A;
     const int nw = W ? W : 2 * a.w.m;
     const int m = nw / 2;
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
@@ -894,45 +1026,44 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
         for (int b0 = 0; b0 < a.batch; b0 += a.batch_smem) {
             const int nb = min(a.batch_smem, a.batch - b0);
             if (!stage_box<T, D>(&tmap, a, box, box_cells, slot, org, wrap, b0, nb, &bar, phase)) {
-                mbar_wait_bounded(&bar, phase ^ 1u, a.err);   // let the copy in flight land
+                if (!a.stall) mbar_wait_bounded(&bar, phase ^ 1u, a.err);   // let the copy in flight land
                 return;
             }
-            for (int j = threadIdx.x; j < wi.count; j += blockDim.x) {
-                const long long i = static_cast<long long>(wi.start) + j;
-                T tau[3];
-                int lb[3] = {0, 0, 0};
-                node_setup<T, D>(a.xs, i, a.g, org, tau, lb, m);
-                const long long dst = a.perm[i];
-                if (!a.wfac && wk == WK_SINH && D >= 2 && nb == 1) {
-                    T w1[A], w2[A];
-                    tap_weights<T, W, WK_SINH>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W, WK_SINH>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] =
-                        a.comp ? contract_lazy0<T, D, W, WK_SINH, true>(box, a.g, lb, tau[0], kind_sin<T, WK_SINH>(tau[0], a.w),
-                                                                        w1, w2, a.w, nw)
-                               : contract_lazy0<T, D, W, WK_SINH>(box, a.g, lb, tau[0], kind_sin<T, WK_SINH>(tau[0], a.w),
-                                                                  w1, w2, a.w, nw);
-                    continue;
+            // FP32: one thread per pair head, a node and, when it has one, its
+            // same-cell partner, which share every box load; FP64 (whose
+            // register budget a second node's weights would exceed): one
+            // thread per node
+            const bool pairs = sizeof(T) == 4 && a.heads != nullptr;
+            const int nh = pairs ? static_cast<int>(a.nheads[item]) : wi.count;
+            for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+                const uint32_t hv = pairs ? a.heads[wi.start + h] : static_cast<uint32_t>(wi.start + h);
+                const long long ia = static_cast<long long>(hv & 0x7FFFFFFFu);
+                const bool two = (hv >> 31) != 0;
+                const long long ib = two ? ia + 1 : ia;
+                T taua[3], taub[3];
+                int lb[3] = {0, 0, 0}, lbb[3] = {0, 0, 0};
+                node_setup<T, D>(a.xs, ia, a.g, org, taua, lb, m);
+                node_setup<T, D>(a.xs, ib, a.g, org, taub, lbb, m);   // same cell: lbb = lb
+                const long long da = a.perm[ia], db = a.perm[ib];
+                if constexpr (D >= 2 && sizeof(T) == 4) {
+                    if (!a.wfac && nb == 1 && (wk == WK_SINH || wk == WK_CSINH || wk == WK_TABLE)) {
+                        C2<T> fa, fb;
+                        if (wk == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
+                        else if (wk == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
+                        else interp_pair<T, D, W, WK_TABLE>(a, box, lb, taua, taub, nw, fa, fb);
+                        a.fout[static_cast<long long>(b0) * a.N + da] = fa;
+                        if (two) a.fout[static_cast<long long>(b0) * a.N + db] = fb;
+                        continue;
+                    }
                 }
-                if (!a.wfac && wk == WK_CSINH && D >= 2 && nb == 1) {
-                    T w1[A], w2[A];
-                    tap_weights<T, W, WK_CSINH>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W, WK_CSINH>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] =
-                        a.comp ? contract_lazy0<T, D, W, WK_CSINH, true>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw)
-                               : contract_lazy0<T, D, W, WK_CSINH>(box, a.g, lb, tau[0], T(0), w1, w2, a.w, nw);
-                    continue;
+                if constexpr (D >= 2 && sizeof(T) == 8) {
+                    if (!a.wfac && nb == 1 && (wk == WK_SINH || wk == WK_CSINH || wk == WK_TABLE)) {
+                        a.fout[static_cast<long long>(b0) * a.N + da] = interp_single<T, D, W>(a, box, lb, taua, wk, nw);
+                        continue;
+                    }
                 }
-                if (!a.wfac && wk == WK_TABLE && D >= 2 && nb == 1) {
-                    T w1[A], w2[A];
-                    tap_weights<T, W, WK_TABLE>(tau[1], a.w, w1);
-                    if (D > 2) tap_weights<T, W, WK_TABLE>(tau[2], a.w, w2);
-                    a.fout[static_cast<long long>(b0) * a.N + dst] =
-                        a.comp ? contract_lazy0<T, D, W, WK_TABLE, true>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw)
-                               : contract_lazy0<T, D, W, WK_TABLE>(box, a.g, lb, tau[0], FM<T>::sinpi(tau[0]), w1, w2, a.w, nw);
-                    continue;
-                }
-                interp_node_general<T, D, W>(a, box, slot, lb, tau, wk, b0, nb, i, dst);
+                interp_node_general<T, D, W>(a, box, slot, lb, taua, wk, b0, nb, ia, da);
+                if (two) interp_node_general<T, D, W>(a, box, slot, lbb, taub, wk, b0, nb, ib, db);
             }
             __syncthreads();
         }
@@ -1382,6 +1513,171 @@ __global__ void __launch_bounds__(512, 1) spread3_kernel(const TapArgs<T> a) {
     }
 }
 
+// d = 3 spreading, column-owner form (FP32, 8 x 8 x 8 tiles, W = 2m <= 16).
+// Lane (c1, c2) of the block owns box column (c1, c2) and keeps its R cells
+// along dimension 0 in registers for the whole work item; warp w owns the
+// patch of 4 x 8 columns at (4 (w / P2), 8 (w mod P2)).  The item's nodes
+// go through node tables of C nodes:
+//  phase A: one thread per (node, dimension) writes the node's 2m window
+//    values of that dimension at their box positions, zero elsewhere
+//    (dimension 0: R rows; dimensions 1, 2: one value per lane column), and
+//    the dimension-0 thread its input value and the mask of the warps whose
+//    patch meets the node's 2m x 2m window of columns;
+//  phase B: every warp in a node's mask adds g * w1[c1] * w2[c2] * w0[q] to
+//    its R registers, one packed FMA per row (lanes outside the window add
+//    zero); two nodes per step.
+// Two tables alternate: the threads fill the next table (phase A) as soon
+// as they are done reading the current one (phase B), with one block barrier
+// per table.  Each box value is the sum of its nodes' contributions in the
+// item's node order, formed by one lane: no atomics, no fixed point, and the
+// result is bitwise reproducible.  The box goes to the item's slot of the
+// ordered flush (gather_kernel), as the other spread kernels' boxes do.
+template <int W>
+__device__ __forceinline__ void spread3c_fill(const TapArgs<float>& a, float* tab, const WorkItem& wi,
+                                              const int (&org)[3], int c0, int b, int wk) {
+    using G = Spread3C<W>;
+    constexpr int m = W / 2;
+    const int nc = min(G::C, wi.count - c0);
+    for (int j = threadIdx.x; j < 3 * nc; j += blockDim.x) {
+        const int k = j / 3, t = j - 3 * k;
+        const long long i = static_cast<long long>(wi.start) + c0 + k;
+        float tau[3];
+        int lb[3] = {0, 0, 0};
+        node_setup<float, 3>(a.xs, i, a.g, org, tau, lb, m);
+        float* row = tab + static_cast<size_t>(k) * G::ROW;
+        const int off = (t == 0) ? 0 : (t == 1) ? G::O1 : G::O2;
+        const int len = (t == 0) ? G::RP : (t == 1) ? 4 * G::P1 : 8 * G::P2;
+        const int lbt = (t == 0) ? lb[0] : (t == 1) ? lb[1] : lb[2];
+        const float taut = (t == 0) ? tau[0] : (t == 1) ? tau[1] : tau[2];
+        float* dst = row + off;
+        for (int q = 0; q < len; ++q)
+            if (q < lbt || q >= lbt + W) dst[q] = 0.0f;
+        if (a.wfac) {   // stored factors (step 0b)
+            const float* src = a.wfac + i * a.wstride + t * W;
+#pragma unroll
+            for (int q = 0; q < W; ++q) dst[lbt + q] = src[q];
+        } else {
+            tap_weights_to<float, W>(dst + lbt, wk, taut, a.w);
+        }
+        if (t == 0) {
+            const float2 gv = a.fin[static_cast<long long>(b) * a.N + a.perm[i]];
+            unsigned mask = 0;
+            for (int r1 = lb[1] / 4; r1 <= (lb[1] + W - 1) / 4 && r1 < G::P1; ++r1)
+                for (int r2 = lb[2] / 8; r2 <= (lb[2] + W - 1) / 8 && r2 < G::P2; ++r2)
+                    mask |= 1u << (r1 * G::P2 + r2);
+            *reinterpret_cast<float4*>(row + G::OM) = make_float4(gv.x, gv.y, __uint_as_float(mask), 0.0f);
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void spread3c_add(float2 (&acc)[Spread3C<W>::R], const float* row, float2 gw) {
+    using G = Spread3C<W>;
+#pragma unroll
+    for (int q = 0; q < G::RP; q += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(row + q);
+        acc[q] = cfma(gw, v.x, acc[q]);
+        if (q + 1 < G::R) acc[q + 1] = cfma(gw, v.y, acc[q + 1]);
+        if (q + 2 < G::R) acc[q + 2] = cfma(gw, v.z, acc[q + 2]);
+        if (q + 3 < G::R) acc[q + 3] = cfma(gw, v.w, acc[q + 3]);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void spread3c_add2(float2 (&acc)[Spread3C<W>::R], const float* ra, float2 ga,
+                                              const float* rb, float2 gb) {
+    using G = Spread3C<W>;
+#pragma unroll
+    for (int q = 0; q < G::RP; q += 4) {
+        const float4 va = *reinterpret_cast<const float4*>(ra + q);
+        const float4 vb = *reinterpret_cast<const float4*>(rb + q);
+        acc[q] = cfma(gb, vb.x, cfma(ga, va.x, acc[q]));
+        if (q + 1 < G::R) acc[q + 1] = cfma(gb, vb.y, cfma(ga, va.y, acc[q + 1]));
+        if (q + 2 < G::R) acc[q + 2] = cfma(gb, vb.z, cfma(ga, va.z, acc[q + 2]));
+        if (q + 3 < G::R) acc[q + 3] = cfma(gb, vb.w, cfma(ga, va.w, acc[q + 3]));
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(Spread3C<W>::THREADS, 1) spread3c_kernel(const TapArgs<float> a) {
+    using G = Spread3C<W>;
+    constexpr int R = G::R, C = G::C, ROW = G::ROW;
+    constexpr int box_cells = R * G::B1 * G::B2;
+    extern __shared__ __align__(16) float s_tab[];   // two tables of C rows of ROW floats
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c1 = 4 * (warp / G::P2) + (lane >> 3), c2 = 8 * (warp % G::P2) + (lane & 7);   // this lane's column
+    const bool owner = c1 < G::B1 && c2 < G::B2;
+    const unsigned wbit = 1u << warp;
+    const int wk = weight_kind(a.w);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    for (int b = 0; b < a.batch; ++b) {
+        int item = blockIdx.x;
+        if (item >= a.n_work) return;
+        WorkItem wi = a.work[item];
+        int org[3] = {0, 0, 0};
+        tile_origin<3>(a.g, wi.tile, periodic, org);
+        int c0 = 0, buf = 0;
+        float2 acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        spread3c_fill<W>(a, s_tab, wi, org, c0, b, wk);
+        __syncthreads();
+        while (true) {
+            // ---- phase B on table `buf`: nodes c0 .. c0 + nc - 1 of the item
+            const float* tab = s_tab + static_cast<size_t>(buf) * C * ROW;
+            const int nc = min(C, wi.count - c0);
+            int k = 0;
+#pragma unroll 1
+            for (; k + 1 < nc; k += 2) {
+                const float* ra = tab + static_cast<size_t>(k) * ROW;
+                const float* rb = ra + ROW;
+                const float4 ma = *reinterpret_cast<const float4*>(ra + G::OM);
+                const float4 mb = *reinterpret_cast<const float4*>(rb + G::OM);
+                const bool ina = (__float_as_uint(ma.z) & wbit) != 0, inb = (__float_as_uint(mb.z) & wbit) != 0;
+                if (!ina && !inb) continue;
+                const float wa = ina ? ra[G::O1 + c1] * ra[G::O2 + c2] : 0.0f;
+                const float wb = inb ? rb[G::O1 + c1] * rb[G::O2 + c2] : 0.0f;
+                const float2 ga = make_float2(ma.x * wa, ma.y * wa), gb = make_float2(mb.x * wb, mb.y * wb);
+                if (ina && inb) spread3c_add2<W>(acc, ra, ga, rb, gb);
+                else if (ina) spread3c_add<W>(acc, ra, ga);
+                else spread3c_add<W>(acc, rb, gb);
+            }
+            if (k < nc) {
+                const float* ra = tab + static_cast<size_t>(k) * ROW;
+                const float4 ma = *reinterpret_cast<const float4*>(ra + G::OM);
+                if (__float_as_uint(ma.z) & wbit) {
+                    const float wa = ra[G::O1 + c1] * ra[G::O2 + c2];
+                    spread3c_add<W>(acc, ra, make_float2(ma.x * wa, ma.y * wa));
+                }
+            }
+            // ---- next table: the item's next nodes, or the next item
+            int nitem = item, nc0 = c0 + C;
+            if (nc0 >= wi.count) {
+                if (owner) {
+                    float2* dst = a.part + (static_cast<long long>(item) * a.batch + b) * box_cells + c1 * G::B2 + c2;
+#pragma unroll
+                    for (int q = 0; q < R; ++q) dst[q * G::B1 * G::B2] = acc[q];
+                }
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc[q] = make_float2(0.0f, 0.0f);
+                nitem = item + gridDim.x;
+                nc0 = 0;
+            }
+            if (nitem >= a.n_work) break;
+            if (nitem != item) {
+                wi = a.work[nitem];
+                tile_origin<3>(a.g, wi.tile, periodic, org);
+            }
+            item = nitem;
+            c0 = nc0;
+            buf ^= 1;
+            spread3c_fill<W>(a, s_tab + static_cast<size_t>(buf) * C * ROW, wi, org, c0, b, wk);
+            __syncthreads();
+        }
+        __syncthreads();   // before the next batch entry refills table 0
+    }
+}
+
 // d = 1 spreading.  Nodes are staged `sub` at a time (weights and the
 // pre-scaled inputs in shared memory); runs of nodes in one cell share their
 // 2m taps.  A warp takes a run: lane l owns tap c = l mod 2m and row group
@@ -1587,7 +1883,7 @@ __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_con
         for (int b0 = 0; b0 < a.batch; b0 += a.batch_smem) {
             const int nb = min(a.batch_smem, a.batch - b0);
             if (!stage_box<T, D>(&tmap, a, box, box_cells, slot, org, wrap, b0, nb, &bar, phase)) {
-                mbar_wait_bounded(&bar, phase ^ 1u, a.err);
+                if (!a.stall) mbar_wait_bounded(&bar, phase ^ 1u, a.err);   // let the copy in flight land
                 return;
             }
             for (int j = threadIdx.x; j < wi.count; j += blockDim.x) {
@@ -1657,12 +1953,23 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         p->launches++;
         return check_cuda(p, cudaGetLastError(), "factor kernel launch");
     }
+    int threads_launch = threads;
+    if constexpr (D == 3 && sizeof(T) == 4 && W >= 4 && W <= 16) {
+        if (kind == TAP_SPREAD && spread3c_applies(3, true, W / 2, p->geom.T)) {
+            using G = Spread3C<W>;
+            if (args.g.box[0] != G::R || args.g.box[1] != G::B1 || args.g.box[2] != G::B2)
+                return fail(p, NFFTBL_EINTERNAL, "column-owner spreading: unexpected box shape");
+            fn = reinterpret_cast<void*>(spread3c_kernel<W>);
+            threads_launch = G::THREADS;
+            smem = G::SMEM;
+        }
+    }
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                           static_cast<int>(smem)),
                                   "tap smem attribute");
     if (st != NFFTBL_OK) return st;
     int occ = 0;
-    st = check_cuda(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem), "occupancy");
+    st = check_cuda(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads_launch, smem), "occupancy");
     if (st != NFFTBL_OK) return st;
     if (occ < 1) return fail(p, NFFTBL_EUNSUPPORTED, "tap kernel does not fit on an SM");
     const long long want = static_cast<long long>(occ) * p->num_sms;
@@ -1675,7 +1982,10 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     else if (kind == TAP_SPREAD) {
         if constexpr (D == 1) spread1_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
         else if constexpr (D == 2) spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
-        else spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
+        else if (threads_launch != threads) {
+            if constexpr (sizeof(T) == 4 && W >= 4 && W <= 16)
+                spread3c_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
+        } else spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
     }
     else
         node_grad_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
