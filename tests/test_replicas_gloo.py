@@ -80,5 +80,10 @@ def test_reference_arm_line_on_rank_0():
         assert key in line, key
     assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    # the same workload object as the GPU arm's line (same sample size for the oracle in both)
+    d, M, m = (bench.CONFIGS[bench.DEFAULT_CONFIG][k] for k in (0, 1, 2))
+    assert line["config"] == bench.workload_config(bench.DEFAULT_CONFIG, bench.default_beta(m), 1)
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert f"first {bench.ORACLE_SAMPLE[d]} of the" in line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
