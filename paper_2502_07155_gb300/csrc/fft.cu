@@ -282,6 +282,14 @@ __device__ __forceinline__ void dft8(C2<T> (&c)[8]) {
     dft4(b, c[1], c[3], c[5], c[7]);
 }
 
+// Position of element x of a line in shared memory: the low four bits are
+// XOR-ed with bits 3..6, a permutation inside each block of 16 elements.
+// With it the reads and writes of every Stockham stage below, and the
+// consecutive accesses of the load and store loops, touch 16 different
+// 8-byte bank pairs per half warp (checked for L = 64 .. 4096); without it
+// the first stage's writes (stride R) are 8-way bank conflicts.
+__device__ __forceinline__ int swz(int x) { return x ^ ((x >> 3) & 15); }
+
 // One Stockham stage of radix R and span S over W lines of length L: butterfly
 // i (k = i mod S) reads i + j L/R, multiplies input j by w^(j k L/(R S)) and
 // writes output q to (i - k) R + k + q S.
@@ -297,10 +305,11 @@ __device__ __forceinline__ void pow2_stage(const C2<T>* __restrict__ src, C2<T>*
         const int i = b & (NB - 1);
         const int k = i & (S - 1);
         const CT* s = src + w * pitch;
-        CT* dd = dst + w * pitch + (i - k) * R + k;
+        CT* dl = dst + w * pitch;
+        const int d0 = (i - k) * R + k;
         CT c[8];
 #pragma unroll
-        for (int j = 0; j < R; ++j) c[j] = s[i + j * NB];
+        for (int j = 0; j < R; ++j) c[j] = s[swz(i + j * NB)];
         if (S > 1) {
             const int e = k * TSTEP;
 #pragma unroll
@@ -324,7 +333,7 @@ __device__ __forceinline__ void pow2_stage(const C2<T>* __restrict__ src, C2<T>*
             c[1] = cmake<T>(a0.x - c[1].x, a0.y - c[1].y);
         }
 #pragma unroll
-        for (int q = 0; q < R; ++q) dd[q * S] = c[q];
+        for (int q = 0; q < R; ++q) dl[swz(d0 + q * S)] = c[q];
     }
 }
 
@@ -390,7 +399,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pow2_kernel(const C2<T>* __re
         const int nz = zhi - zlo;
         for (int idx = tid; idx < W * nz; idx += bd) {
             const int w = (W == 1) ? 0 : idx / nz;
-            bufA[w * pitch + zlo + idx - w * nz] = cmake<T>(T(0), T(0));
+            bufA[w * pitch + swz(zlo + idx - w * nz)] = cmake<T>(T(0), T(0));
         }
     }
     constexpr int kBatch = 8;
@@ -424,7 +433,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_pow2_kernel(const C2<T>* __re
                     val.y *= f[u];
                     q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
                 }
-                bufA[w * pitch + q] = val;
+                bufA[w * pitch + swz(q)] = val;
             }
         }
     }
@@ -443,10 +452,10 @@ __global__ void __launch_bounds__(kFftThreads) fft_pow2_kernel(const C2<T>* __re
                                          : (o0 * n_out + p) * static_cast<long long>(inner) + i0 + w;
         CT v;
         if (!ADJ) {
-            v = src[w * pitch + p];
+            v = src[w * pitch + swz(p)];
         } else {
             const int q = (p < M / 2) ? (L - M / 2 + p) : (p - M / 2);
-            v = src[w * pitch + q];
+            v = src[w * pitch + swz(q)];
             const T f = fac[p];
             v.x *= f;
             v.y *= f;
