@@ -95,6 +95,13 @@ typedef struct {
     int precorrect;         /* 1 (default): D_psihat = diag(1/(|I_L| psi_hat(k))) of Eq. 4.9
                                (D of Eq. 2.2); 0: D = I, the approximation of Section 5
                                that uses |I_L| psi_hat(k) ~ 1 (an ablation)             */
+    int weights;            /* tap weights psi(x_j - l/L) of the spreading (transposed
+                               step 3) in FP32 plans with m <= 8: 0 (default) the window's
+                               closed form per tap; 1: one polynomial per tap in the node's
+                               offset, fitted in FP64 when the plan is made and kept only
+                               if it is accurate to 3e-7 of the largest weight (FP32
+                               evaluation included).  The interpolation and the node
+                               derivative always use the closed form                    */
 } nfftbl_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -251,6 +258,9 @@ typedef struct {
     int64_t n_tiles;
     int64_t n_work;         /* work items (tile, chunk) after set_nodes              */
     int key_bits;           /* bits of the binning key                               */
+    int poly_weights;       /* 1: the short sums use the per-tap weight polynomials     */
+    double poly_err;        /* their largest error relative to the largest weight (0 if
+                               no fit was made)                                          */
 } nfftbl_info;
 
 /* The plan's parameters (after defaults: L_t, beta, tile extents) and, once

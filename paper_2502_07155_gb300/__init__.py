@@ -54,7 +54,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("method", ctypes.c_int), ("beta", ctypes.c_double),
                 ("batch", ctypes.c_int), ("table", ctypes.POINTER(ctypes.c_double)),
                 ("table_len", ctypes.c_int), ("tile", ctypes.c_int * 3), ("nodes_per_item", ctypes.c_int),
-                ("factors", ctypes.c_int), ("precorrect", ctypes.c_int)]
+                ("factors", ctypes.c_int), ("precorrect", ctypes.c_int), ("weights", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -62,7 +62,7 @@ class _Info(ctypes.Structure):
                 ("precision", ctypes.c_int), ("method", ctypes.c_int), ("window", ctypes.c_int),
                 ("batch", ctypes.c_int), ("beta", ctypes.c_double), ("tile", ctypes.c_int * 3),
                 ("n_nodes", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("n_work", ctypes.c_int64),
-                ("key_bits", ctypes.c_int)]
+                ("key_bits", ctypes.c_int), ("poly_weights", ctypes.c_int), ("poly_err", ctypes.c_double)]
 
 
 _lib = None
@@ -170,13 +170,15 @@ class Plan:
     'classic'), ``beta`` (None = default), ``batch``, ``table`` (values on
     u in [0, 1] for the table window), ``tile``, ``nodes_per_item``,
     ``factors`` (keep the d x 2m window factors per node from set_nodes),
-    ``precorrect`` (False: D = I, Section 5's approximation |I_L| psi_hat ~ 1).
+    ``precorrect`` (False: D = I, Section 5's approximation |I_L| psi_hat ~ 1),
+    ``weights`` ('closed': the window's closed form, the default; 'poly':
+    per-tap polynomial weights in the FP32 spreading where they are accurate).
     """
 
     def __init__(self, d: int, M, sigma: float = 2.0, m: int = 6, window: str = "sinh",
                  precision: str = "f32", method: str = "shannon", beta: float | None = None,
                  batch: int = 1, table=None, tile=None, nodes_per_item: int | None = None,
-                 factors: bool = False, precorrect: bool = True):
+                 factors: bool = False, precorrect: bool = True, weights: str = "closed"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("nfftbl needs a CUDA device; there is no CPU fallback")
@@ -205,6 +207,7 @@ class Plan:
             o.nodes_per_item = int(nodes_per_item)
         o.factors = 1 if factors else 0
         o.precorrect = 1 if precorrect else 0
+        o.weights = {"closed": 0, "poly": 1}[weights]
         Marr = (ctypes.c_int * 3)(*(Ms + [0] * (3 - d)))
         h = ctypes.c_void_p()
         st = self._lib.nfftbl_plan(ctypes.byref(h), d, Marr, float(sigma), int(m), _WINDOWS[window], ctypes.byref(o))
@@ -400,7 +403,7 @@ class Plan:
         return {"d": inf.d, "M": list(inf.M), "L": list(inf.L), "m": inf.m, "precision": inf.precision,
                 "method": inf.method, "window": inf.window, "batch": inf.batch, "beta": inf.beta,
                 "tile": list(inf.tile), "n_nodes": inf.n_nodes, "n_tiles": inf.n_tiles, "n_work": inf.n_work,
-                "key_bits": inf.key_bits}
+                "key_bits": inf.key_bits, "poly_weights": inf.poly_weights, "poly_err": inf.poly_err}
 
     def factors(self, t: int) -> np.ndarray:
         """d_t(k) = 1/(L_t psi_hat_t(k)), k in I_{M_t} (host copy)."""

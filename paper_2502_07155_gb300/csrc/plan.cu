@@ -141,6 +141,9 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
     a.wstride = factor_stride(p);
     a.wfac = p->wfac_valid ? static_cast<const T*>(p->wfac.p) : nullptr;
     a.w.tcoef = (sizeof(T) == 4 && p->window == NFFTBL_WIN_TABLE) ? static_cast<const float4*>(p->table_coef.p) : nullptr;
+    a.w.poly = (sizeof(T) == 4 && p->poly_ok) ? 1 : 0;
+    a.w.poly_edge_sqrt = p->poly_edge_sqrt;
+    std::memcpy(a.w.pc, p->poly_coef, sizeof(a.w.pc));
     a.batch = p->batch;
     const size_t bb = (static_cast<size_t>(box_cells(p->geom)) * sizeof(C2<T>) + 127) / 128 * 128;
     a.batch_smem = static_cast<int>(std::max<size_t>(1, std::min<size_t>(p->batch, kBoxBudget / bb)));
@@ -372,6 +375,120 @@ using namespace nfftbl;
 
 extern "C" {
 
+namespace nfftbl {
+namespace {
+
+// Catmull-Rom value of a window table at u in [0, 1] (the rule the kernels
+// use: ghost values v_{-1} = v_1, v_{n+1} = 2 v_n - v_{n-1}), in FP64.
+double table_value(const std::vector<double>& v, double u) {
+    const int n = static_cast<int>(v.size()) - 1;
+    const double s = std::min(std::max(u, 0.0), 1.0) * n;
+    int i = static_cast<int>(std::floor(s));
+    i = std::min(std::max(i, 0), n - 1);
+    const double t = s - i;
+    const double p0 = (i == 0) ? v[1] : v[i - 1], p1 = v[i], p2 = v[i + 1];
+    const double p3 = (i + 2 <= n) ? v[i + 2] : 2.0 * v[n] - v[n - 1];
+    return 0.5 * (2.0 * p1 + (p2 - p0) * t + (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3) * t * t +
+                  (3.0 * p1 - p0 - 3.0 * p2 + p3) * t * t * t);
+}
+
+// The one-dimensional short-sum kernel at the tap offset delta = L x - l
+// (grid units), in FP64: sinc(pi delta) phi(delta / L) for the Shannon
+// method, phi(delta / L) for the classical NFFT; zero for |delta| >= m.
+double kernel_value(const nfftbl_plan_s* p, double delta) {
+    const double r = delta / p->m;
+    const double q = (1.0 - r) * (1.0 + r);
+    if (!(q > 0.0)) return 0.0;
+    double phi;
+    if (p->window == NFFTBL_WIN_SINH) phi = std::sinh(p->beta * std::sqrt(q)) / std::sinh(p->beta);
+    else if (p->window == NFFTBL_WIN_CKB)
+        phi = (std::cyl_bessel_i(0.0, p->beta * std::sqrt(q)) - 1.0) / (std::cyl_bessel_i(0.0, p->beta) - 1.0);
+    else phi = table_value(p->table_host, std::fabs(r));
+    if (p->method == NFFTBL_CLASSIC) return phi;
+    const double sinc = (delta == 0.0) ? 1.0 : std::sin(M_PI * delta) / (M_PI * delta);
+    return sinc * phi;
+}
+
+// Per-tap weight polynomials of an FP32 plan with m <= 8: tap a (offset
+// delta = tau + m - 1 - a, tau in [0, 1)) as a polynomial of degree
+// kPolyDeg in t = 2 tau - 1, by Chebyshev interpolation in FP64 converted to
+// monomial coefficients.  Windows with a square-root edge (sinh,
+// Kaiser-Bessel) fit the two edge taps divided by sqrt(1 - (delta/m)^2),
+// which removes the edge singularity; the kernels multiply it back.  The fit
+// is checked on a fine grid with the kernels' FP32 Horner evaluation and
+// kept only if its largest error is within kPolyTol of the largest weight.
+void fit_poly(nfftbl_plan_s* p) {
+    p->poly_ok = false;
+    p->poly_err = 0.0;
+    if (p->precision == NFFTBL_F64 || p->m < 2 || p->m > 8 || p->weights_mode != 1) return;
+    const int W = 2 * p->m, D = kPolyDeg;
+    const bool sqrt_edge = p->window == NFFTBL_WIN_SINH || p->window == NFFTBL_WIN_CKB;
+    p->poly_edge_sqrt = sqrt_edge ? 1 : 0;
+    auto edge_q = [&](double delta) {
+        const double r = delta / p->m;
+        return (1.0 - r) * (1.0 + r);
+    };
+    double tk[kPolyDeg + 1];
+    for (int k = 0; k <= D; ++k) tk[k] = std::cos(M_PI * (k + 0.5) / (D + 1));
+    for (int a = 0; a < W; ++a) {
+        const int n = p->m - 1 - a;
+        const bool edge = sqrt_edge && (a == 0 || a == W - 1);
+        double fv[kPolyDeg + 1];
+        for (int k = 0; k <= D; ++k) {
+            const double delta = 0.5 * (tk[k] + 1.0) + n;
+            fv[k] = kernel_value(p, delta) / (edge ? std::sqrt(edge_q(delta)) : 1.0);
+        }
+        // Chebyshev coefficients, then the monomial form of sum_j c_j T_j(t)
+        double cheb[kPolyDeg + 1], mono[kPolyDeg + 1] = {};
+        for (int j = 0; j <= D; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k <= D; ++k) acc += fv[k] * std::cos(M_PI * j * (k + 0.5) / (D + 1));
+            cheb[j] = acc * 2.0 / (D + 1) * (j == 0 ? 0.5 : 1.0);
+        }
+        double tm2[kPolyDeg + 1] = {1.0}, tm1[kPolyDeg + 1] = {0.0, 1.0};   // T_0, T_1
+        mono[0] += cheb[0];
+        if (D >= 1) mono[1] += cheb[1];
+        for (int j = 2; j <= D; ++j) {
+            double tj[kPolyDeg + 1] = {};
+            for (int k = 0; k <= D; ++k) {
+                tj[k] = -tm2[k] + (k > 0 ? 2.0 * tm1[k - 1] : 0.0);
+            }
+            for (int k = 0; k <= D; ++k) mono[k] += cheb[j] * tj[k];
+            for (int k = 0; k <= D; ++k) {
+                tm2[k] = tm1[k];
+                tm1[k] = tj[k];
+            }
+        }
+        for (int k = 0; k < 12; ++k) p->poly_coef[a][k] = (k <= D) ? static_cast<float>(mono[k]) : 0.0f;
+    }
+    // check: FP32 Horner (as the kernels evaluate it) against the FP64 kernel
+    double err = 0.0, big = 0.0;
+    const int G = 2048;
+    for (int a = 0; a < W; ++a) {
+        const int n = p->m - 1 - a;
+        const bool edge = sqrt_edge && (a == 0 || a == W - 1);
+        for (int g = 0; g <= G; ++g) {
+            const float tau = static_cast<float>(g) / G * 0.99999994f;
+            const float t = std::fma(2.0f, tau, -1.0f);
+            float v = p->poly_coef[a][D];
+            for (int k = D - 1; k >= 0; --k) v = std::fma(v, t, p->poly_coef[a][k]);
+            if (edge) {
+                const float r = (tau + static_cast<float>(n)) * static_cast<float>(1.0 / p->m);
+                const float q = std::fma(-r, r, 1.0f);
+                v = (q > 1e-30f) ? v * std::sqrt(q) : 0.0f;
+            }
+            const double ref = kernel_value(p, static_cast<double>(tau) + n);
+            err = std::max(err, std::fabs(static_cast<double>(v) - ref));
+            big = std::max(big, std::fabs(ref));
+        }
+    }
+    p->poly_err = (big > 0.0) ? err / big : err;
+    p->poly_ok = p->poly_err <= kPolyTol;
+}
+
+}  // namespace
+}  // namespace nfftbl
+
 void nfftbl_default_opts(nfftbl_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
@@ -381,6 +498,7 @@ void nfftbl_default_opts(nfftbl_opts* o) {
     o->batch = 1;
     o->factors = 0;
     o->precorrect = 1;
+    o->weights = 0;
 }
 
 nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma, int m, int window,
@@ -400,6 +518,7 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     if (o.method < 0 || o.method > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "unknown method");
     if (o.factors < 0 || o.factors > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "factors must be 0 or 1");
     if (o.precorrect < 0 || o.precorrect > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "precorrect must be 0 or 1");
+    if (o.weights < 0 || o.weights > 1) return plan_fail(nullptr, NFFTBL_EINVAL, "weights must be 0 or 1");
     if (o.batch < 1) return plan_fail(nullptr, NFFTBL_EINVAL, "batch must be >= 1");
     if (window == NFFTBL_WIN_TABLE && (!o.table || o.table_len < 3))
         return plan_fail(nullptr, NFFTBL_EINVAL, "table window needs a table of >= 3 values");
@@ -493,6 +612,8 @@ nfftbl_status nfftbl_plan(nfftbl_plan_t* out, int d, const int* M, double sigma,
     p->n_tiles = 1;
     for (int t = 0; t < d; ++t) p->n_tiles *= g.nt[t];
     if (window == NFFTBL_WIN_TABLE) p->table_host.assign(o.table, o.table + o.table_len);
+    p->weights_mode = o.weights;
+    fit_poly(p);
 
     nfftbl_status st;
     if ((st = check_cuda(p, cudaGetDevice(&p->device), "cudaGetDevice")) != NFFTBL_OK) return plan_fail(p, st, "");
@@ -836,6 +957,8 @@ nfftbl_status nfftbl_get_info(nfftbl_plan_t p, nfftbl_info* info) {
     info->n_tiles = p->n_tiles;
     info->n_work = p->n_work;
     info->key_bits = p->key_bits;
+    info->poly_weights = p->poly_ok ? 1 : 0;
+    info->poly_err = p->poly_err;
     return NFFTBL_OK;
 }
 
@@ -887,6 +1010,7 @@ nfftbl_status nfftbl_set_window_table(nfftbl_plan_t p, const double* table_dev, 
     if (p->window != NFFTBL_WIN_TABLE) return fail(p, NFFTBL_ESTATE, "plan does not use a table window");
     if (table_len != static_cast<int>(p->table_host.size()))
         return fail(p, NFFTBL_EINVAL, "table length differs from the plan's");
+    p->poly_ok = false;   // fitted to the host table the plan was made with: the closed form from here on
     const bool dbl = p->precision == NFFTBL_F64;
     void* t64 = dbl ? p->table_dev.p : p->table_dev64.p;
     nfftbl_status st = check_cuda(p, cudaMemcpyAsync(t64, table_dev, table_len * sizeof(double),

@@ -26,7 +26,20 @@ struct WinParams {
     const T* table;    // window table on u in [0, 1] (table window), device
     int table_n;       // number of intervals (table has table_n + 1 values)
     const float4* tcoef;   // FP32 plans: per interval the Catmull-Rom cubic c0 + c1 t + c2 t^2 + c3 t^3
+    // FP32 plans with a compile-time truncation: tap a's weight as a
+    // polynomial in t = 2 tau - 1 of degree kPolyDeg (coefficients of t^0 ..
+    // t^kPolyDeg), fitted on the host; for windows with a square-root edge
+    // (sinh, Kaiser-Bessel) the edge taps' polynomial is multiplied by
+    // sqrt(1 - (delta/m)^2).  poly = 0: the window's closed form instead.
+    int poly;
+    int poly_edge_sqrt;
+    float pc[16][12];
 };
+
+constexpr int kPolyDeg = 10;   // degree of the per-tap weight polynomials
+// Largest tolerated error of a fitted tap weight, FP32 evaluation included,
+// relative to the largest weight: above it the plan keeps the closed form.
+constexpr double kPolyTol = 3e-7;
 
 // Geometry of the node tiles and of the shared-memory boxes around them.
 struct TileGeom {
@@ -281,6 +294,11 @@ struct nfftbl_plan_s {
     int key_bits = 0;
 
     nfftbl::DeviceBuf lw_f, lw_h, lw_marg, lw_dpsi;   // learned-window loss/gradient scratch
+    int weights_mode = 0;                 // opts.weights
+    bool poly_ok = false;                 // per-tap weight polynomials fitted (FP32 plans)
+    int poly_edge_sqrt = 0;
+    float poly_coef[16][12] = {};
+    double poly_err = 0.0;                // their largest error (FP32 evaluation) on a fine grid
     nfftbl::DeviceBuf err;                // device error word
     int* err_host = nullptr;              // pinned mirror
     unsigned long long wait_ns = nfftbl::kWaitLimitNs;   // limit of the box-staging waits

@@ -117,10 +117,25 @@ __device__ __forceinline__ T table_deriv(const T* __restrict__ v, int n, T u) {
     return dt * static_cast<T>(n);
 }
 
+// The fields of WinParams the out-of-line window routines read (passed by
+// value: small, unlike the whole parameter block with its polynomials).
+template <typename T>
+struct WinLite {
+    int window;
+    T inv_m, beta, c_norm;
+    const T* table;
+    int table_n;
+};
+
+template <typename T>
+__device__ __forceinline__ WinLite<T> win_lite(const WinParams<T>& w) {
+    return WinLite<T>{w.window, w.inv_m, w.beta, w.c_norm, w.table, w.table_n};
+}
+
 // Kaiser-Bessel and tabulated windows, kept out of line: they are rare and
 // their code would otherwise be inlined into every unrolled tap.
 template <typename T>
-__device__ __noinline__ T win_phi_other(T delta, const WinParams<T> w) {
+__device__ __noinline__ T win_phi_other(T delta, const WinLite<T> w) {
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
@@ -129,7 +144,7 @@ __device__ __noinline__ T win_phi_other(T delta, const WinParams<T> w) {
 }
 
 template <typename T>
-__device__ __noinline__ T win_dphi_other(T delta, const WinParams<T> w) {
+__device__ __noinline__ T win_dphi_other(T delta, const WinLite<T> w) {
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
@@ -144,7 +159,7 @@ __device__ __noinline__ T win_dphi_other(T delta, const WinParams<T> w) {
 // Window Phi(delta) = phi(delta / L) for a tap offset delta = L x - l in grid units.
 template <typename T>
 __device__ __forceinline__ T win_phi(T delta, const WinParams<T>& w) {
-    if (w.window != NFFTBL_WIN_SINH) return win_phi_other(delta, w);
+    if (w.window != NFFTBL_WIN_SINH) return win_phi_other(delta, win_lite(w));
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
@@ -159,7 +174,7 @@ __device__ __forceinline__ T win_phi(T delta, const WinParams<T>& w) {
 // the sinh / Kaiser-Bessel windows meets a vanishing factor there).
 template <typename T>
 __device__ __forceinline__ T win_dphi(T delta, const WinParams<T>& w) {
-    if (w.window != NFFTBL_WIN_SINH) return win_dphi_other(delta, w);
+    if (w.window != NFFTBL_WIN_SINH) return win_dphi_other(delta, win_lite(w));
     const T r = delta * w.inv_m;
     const T q = (T(1) - r) * (T(1) + r);
     if (!(q > T(0))) return T(0);
@@ -211,18 +226,52 @@ enum : int {
     WK_SINH = 1,        // Shannon method, sinh window
     WK_TABLE = 2,       // Shannon method, tabulated window (the learned phi_theta)
     WK_CSINH = 3,       // classical method (Algorithm 2.1), sinh window
+    WK_POLY = 4,        // FP32, any window and method: the plan's per-tap weight polynomials
 };
 
 // The sine factor the Shannon weights of kind WK take: sin(pi tau), times
 // the sinh window's normalisation for WK_SINH.
 template <typename T, int WK>
 __device__ __forceinline__ T kind_sin(T tau, const WinParams<T>& wp) {
+    if constexpr (WK == WK_POLY || WK == WK_CSINH) return T(0);
     const T s = FM<T>::sinpi(tau);
     return (WK == WK_SINH) ? s * wp.c_norm : s;
 }
 
+// Tap a's weight from the plan's polynomial (WK_POLY): Horner in
+// t = 2 tau - 1 over kPolyDeg + 1 coefficients (operands of the kernel's
+// parameter block when a is a compile-time index), times
+// sqrt(1 - (delta/m)^2) at the two edge taps of a square-root-edged window.
+template <typename T>
+__device__ __forceinline__ T poly_weight(T tau, int a, int m, const WinParams<T>& wp) {
+    if constexpr (sizeof(T) == 4) {
+        const float t = fmaf(2.0f, tau, -1.0f);
+        float v = wp.pc[a][kPolyDeg];
+#pragma unroll
+        for (int k = kPolyDeg - 1; k >= 0; --k) v = fmaf(v, t, wp.pc[a][k]);
+        if (wp.poly_edge_sqrt && (a == 0 || a == 2 * m - 1)) {
+            const float r = (tau + static_cast<float>(m - 1 - a)) * wp.inv_m;
+            const float q = fmaf(-r, r, 1.0f);
+            v = (q > 1e-30f) ? v * (q * rsqrt_approx(q)) : 0.0f;
+        }
+        return v;
+    } else {
+        return T(0);   // (FP64 plans have no polynomials)
+    }
+}
+
+// The weight kind of the window's closed form (the polynomials aside).
+template <typename T>
+__device__ __forceinline__ int closed_kind(const WinParams<T>& w) {
+    if (w.method != NFFTBL_SHANNON) return (w.window == NFFTBL_WIN_SINH) ? WK_CSINH : WK_GENERIC;
+    if (w.window == NFFTBL_WIN_SINH) return WK_SINH;
+    if (w.window == NFFTBL_WIN_TABLE) return WK_TABLE;
+    return WK_GENERIC;
+}
+
 template <typename T>
 __device__ __forceinline__ int weight_kind(const WinParams<T>& w) {
+    if (sizeof(T) == 4 && w.poly) return WK_POLY;
     if (w.method != NFFTBL_SHANNON) return (w.window == NFFTBL_WIN_SINH) ? WK_CSINH : WK_GENERIC;
     if (w.window == NFFTBL_WIN_SINH) return WK_SINH;
     if (w.window == NFFTBL_WIN_TABLE) return WK_TABLE;
@@ -284,7 +333,8 @@ __device__ __forceinline__ T classic_sinh_weight(T tau, int a, int m, const WinP
 // used by the Shannon kinds only.
 template <typename T, int WK>
 __device__ __forceinline__ T fast_weight(T tau, T s, int a, int m, const WinParams<T>& wp) {
-    if constexpr (WK == WK_TABLE) return shannon_table_weight(tau, s, a, m, wp);
+    if constexpr (WK == WK_POLY) return poly_weight(tau, a, m, wp);
+    else if constexpr (WK == WK_TABLE) return shannon_table_weight(tau, s, a, m, wp);
     else if constexpr (WK == WK_CSINH) return classic_sinh_weight(tau, a, m, wp);
     else return shannon_sinh_weight(tau, s, a, m, wp);
 }
@@ -331,7 +381,10 @@ template <typename T, int W>
 __device__ __forceinline__ void tap_weights_to(T* dst, int wk, T tau, const WinParams<T>& wp) {
     const int m = W ? W / 2 : wp.m;
     const int nw = 2 * m;
-    if (wk == WK_SINH) {
+    if (wk == WK_POLY && W != 0) {
+#pragma unroll
+        for (int a = 0; a < TapN<W>::A; ++a) dst[a] = poly_weight(tau, a, m, wp);
+    } else if (wk == WK_SINH) {
         const T s = kind_sin<T, WK_SINH>(tau, wp);
 #pragma unroll 2
         for (int a = 0; a < nw; ++a) dst[a] = shannon_sinh_weight(tau, s, a, m, wp);
@@ -701,8 +754,7 @@ __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ bo
     if constexpr (D == 2) {
         const int pitch = g.box[1];
         const C2<T>* p = box + lb[0] * pitch + lb[1];
-#pragma unroll 2
-        for (int a = 0; a < nw; ++a) {
+        auto row_step = [&](int a) {
             const T w0a = fast_weight<T, WK>(tau0a, s0a, a, m, wp);
             const T w0b = fast_weight<T, WK>(tau0b, s0b, a, m, wp);
             const C2<T>* row = p + a * pitch;
@@ -722,7 +774,9 @@ __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ bo
                 acca = cfma(ra, w0a, acca);
                 accb = cfma(rb, w0b, accb);
             }
-        }
+        };
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) row_step(a);
     } else if constexpr (D == 3) {
         const int p1 = g.box[2];
         const int p0 = g.box[1] * p1;
@@ -982,7 +1036,9 @@ __global__ void __launch_bounds__(256) factor_kernel(const TapArgs<T> a, T* __re
             const T u = mul_rn(static_cast<T>(a.g.L[t]), a.xs[i * D + t]);
             const T tau = u - FM<T>::flr(u);
             T w[A];
-            if (wk == WK_SINH)
+            if (wk == WK_POLY)
+                tap_weights<T, W, WK_POLY>(tau, a.w, w);
+            else if (wk == WK_SINH)
                 tap_weights<T, W, WK_SINH>(tau, a.w, w);
             else if (wk == WK_TABLE)
                 tap_weights<T, W, WK_TABLE>(tau, a.w, w);
@@ -1046,10 +1102,13 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                 node_setup<T, D>(a.xs, ib, a.g, org, taub, lbb, m);   // same cell: lbb = lb
                 const long long da = a.perm[ia], db = a.perm[ib];
                 if constexpr (D >= 2 && sizeof(T) == 4) {
-                    if (!a.wfac && nb == 1 && (wk == WK_SINH || wk == WK_CSINH || wk == WK_TABLE)) {
+                    // (the closed form here: unrolled polynomial weights in registers
+                    // raise this kernel's register count past its occupancy)
+                    const int wkc = closed_kind(a.w);
+                    if (!a.wfac && nb == 1 && (wkc == WK_SINH || wkc == WK_CSINH || wkc == WK_TABLE)) {
                         C2<T> fa, fb;
-                        if (wk == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
-                        else if (wk == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
+                        if (wkc == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
+                        else if (wkc == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
                         else interp_pair<T, D, W, WK_TABLE>(a, box, lb, taua, taub, nw, fa, fb);
                         a.fout[static_cast<long long>(b0) * a.N + da] = fa;
                         if (two) a.fout[static_cast<long long>(b0) * a.N + db] = fb;
@@ -1062,8 +1121,9 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
                         continue;
                     }
                 }
-                interp_node_general<T, D, W>(a, box, slot, lb, taua, wk, b0, nb, ia, da);
-                if (two) interp_node_general<T, D, W>(a, box, slot, lbb, taub, wk, b0, nb, ib, db);
+                // (closed-form weights: see above)
+                interp_node_general<T, D, W>(a, box, slot, lb, taua, closed_kind(a.w), b0, nb, ia, da);
+                if (two) interp_node_general<T, D, W>(a, box, slot, lbb, taub, closed_kind(a.w), b0, nb, ib, db);
             }
             __syncthreads();
         }
@@ -1853,6 +1913,70 @@ __global__ void __launch_bounds__(256, 8) gather_kernel(const TapArgs<T> a) {
     a.grid[idx] = cmake<T>(sr, si);
 }
 
+// The d partial derivatives of one node's short sum in one pass over its
+// taps: dimension t's derivative replaces that dimension's weights by their
+// derivatives (the tensor product rule), so every box value is loaded once
+// and enters each derivative's sum (d = 2: two sums per row; d = 3: the row
+// sums with w2 and dw2 feed three partial sums).  g[t] = d f / d x_t.
+template <typename T, int D, int W>
+__device__ __forceinline__ void contract_grad(const C2<T>* __restrict__ box, const TileGeom& g, const int (&lb)[3],
+                                              const T (&w)[3][TapN<W>::A], const T (&dw)[3][TapN<W>::A], int nw_rt,
+                                              C2<T> (&gr)[3]) {
+    const int nw = W ? W : nw_rt;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) gr[t] = cmake<T>(T(0), T(0));
+    if constexpr (D == 1) {
+        const C2<T>* p = box + lb[0];
+#pragma unroll
+        for (int a = 0; a < TapN<W>::A; ++a)
+            if (a < nw) gr[0] = cfma(p[a], dw[0][a], gr[0]);
+    } else if constexpr (D == 2) {
+        const int pitch = g.box[1];
+        const C2<T>* p = box + lb[0] * pitch + lb[1];
+#pragma unroll 2
+        for (int a = 0; a < nw; ++a) {
+            const C2<T>* row = p + a * pitch;
+            C2<T> r = cmake<T>(T(0), T(0)), rd = cmake<T>(T(0), T(0));
+#pragma unroll
+            for (int b = 0; b < TapN<W>::A; ++b) {
+                if (b < nw) {
+                    const C2<T> v = row[b];
+                    r = cfma(v, w[1][b], r);
+                    rd = cfma(v, dw[1][b], rd);
+                }
+            }
+            gr[0] = cfma(r, dw[0][a], gr[0]);
+            gr[1] = cfma(rd, w[0][a], gr[1]);
+        }
+    } else {
+        const int p1 = g.box[2];
+        const int p0 = g.box[1] * p1;
+        const C2<T>* p = box + lb[0] * p0 + lb[1] * p1 + lb[2];
+        for (int a = 0; a < nw; ++a) {
+            C2<T> m0 = cmake<T>(T(0), T(0)), m1 = m0, m2 = m0;
+#pragma unroll 2
+            for (int b = 0; b < nw; ++b) {
+                const C2<T>* row = p + a * p0 + b * p1;
+                C2<T> r = cmake<T>(T(0), T(0)), rd = cmake<T>(T(0), T(0));
+#pragma unroll
+                for (int c = 0; c < TapN<W>::A; ++c) {
+                    if (c < nw) {
+                        const C2<T> v = row[c];
+                        r = cfma(v, w[2][c], r);
+                        rd = cfma(v, dw[2][c], rd);
+                    }
+                }
+                m0 = cfma(r, w[1][b], m0);
+                m1 = cfma(r, dw[1][b], m1);
+                m2 = cfma(rd, w[1][b], m2);
+            }
+            gr[0] = cfma(m0, dw[0][a], gr[0]);
+            gr[1] = cfma(m1, w[0][a], gr[1]);
+            gr[2] = cfma(m2, w[0][a], gr[2]);
+        }
+    }
+}
+
 // Node gradient: grad_x[j, t] = sum_b Re(conj(gf[b, j]) * d f_{b,j} / d x_{j,t}).
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_constant__ CUtensorMap tmap,
@@ -1899,22 +2023,10 @@ __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_con
                 for (int bb = 0; bb < nb; ++bb) {
                     const CT* bx = box + bb * slot;
                     const CT gf = a.fin[static_cast<long long>(b0 + bb) * a.N + dst];
-                    // partial derivatives: replace one dimension's weights by their derivative
+                    CT dv[3];
+                    contract_grad<T, D, W>(bx, a.g, lb, w, dw, nw, dv);
 #pragma unroll
-                    for (int t = 0; t < D; ++t) {
-                        CT dv;
-                        if (D == 1) {
-                            dv = contract<T, 1, W>(bx, a.g, lb, dw[0], dw[0], dw[0], false, nw);
-                        } else if (D == 2) {
-                            dv = (t == 0) ? contract<T, 2, W>(bx, a.g, lb, dw[0], w[1], w[1], false, nw)
-                                          : contract<T, 2, W>(bx, a.g, lb, w[0], dw[1], dw[1], false, nw);
-                        } else {
-                            dv = (t == 0)   ? contract<T, 3, W>(bx, a.g, lb, dw[0], w[1], w[2], false, nw)
-                                 : (t == 1) ? contract<T, 3, W>(bx, a.g, lb, w[0], dw[1], w[2], false, nw)
-                                            : contract<T, 3, W>(bx, a.g, lb, w[0], w[1], dw[2], false, nw);
-                        }
-                        gsum[t] += gf.x * dv.x + gf.y * dv.y;
-                    }
+                    for (int t = 0; t < D; ++t) gsum[t] += gf.x * dv[t].x + gf.y * dv[t].y;
                 }
 #pragma unroll
                 for (int t = 0; t < D; ++t) {

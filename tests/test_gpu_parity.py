@@ -447,3 +447,36 @@ def test_batch_larger_than_one_shared_memory_group(d, batch, prec):
     gx = to_host(plan.node_grad(to_dev(fh), to_dev(g)))
     plan.sync()
     assert rel_l2(gx, O.node_grad(op, fh, x, g)) < TOL[prec]
+
+
+# --------------------------------------------------------------------------- polynomial tap weights
+
+@pytest.mark.parametrize("d,m,method,window", [(1, 8, "shannon", "sinh"), (2, 6, "shannon", "sinh"),
+                                               (2, 4, "classic", "sinh"), (2, 5, "shannon", "ckb"),
+                                               (3, 4, "shannon", "sinh"), (2, 3, "shannon", "table")])
+def test_polynomial_weights_match_closed_form(d, m, method, window):
+    """FP32 plans made with weights='poly' fit one polynomial per tap; the
+    fit is kept only within 3e-7 of the largest weight.  The forward and
+    adjoint transforms with the polynomials agree with the closed-form
+    weights (the default) and with the oracle at the FP32 tolerance."""
+    M = SHAPES[d][0]
+    tab = O.learned_table(O.mlp_init()) if window == "table" else None
+    x = W.nodes_uniform(2000, d, dtype=np.float32, seed=12)
+    fh = W.fhat_gaussian(M, d, batch=1, dtype=np.complex64, seed=13)
+    g = W.adjoint_input(2000, batch=1, dtype=np.complex64, seed=14)
+    res = {}
+    for wts in ("poly", "closed"):
+        plan = nb.Plan(d, M, 2.0, m, window=window, precision="f32", method=method, table=tab, weights=wts)
+        info = plan.info()
+        if wts == "poly":
+            assert info["poly_weights"] == 1 and 0 < info["poly_err"] <= 3e-7, info
+        else:
+            assert info["poly_weights"] == 0
+        plan.set_nodes(to_dev(x))
+        res[wts] = (to_host(plan.forward(to_dev(fh))), to_host(plan.adjoint(to_dev(g))))
+        plan.sync()
+        op = oracle_plan(plan, table=tab)
+    for k in range(2):
+        assert rel_l2(res["poly"][k], res["closed"][k]) < 2e-6
+    assert rel_l2(res["poly"][0], O.forward(op, fh, x)) < TOL["f32"]
+    assert rel_l2(res["poly"][1], O.adjoint(op, g, x)) < TOL["f32"]
