@@ -1053,6 +1053,44 @@ __global__ void __launch_bounds__(256) factor_kernel(const TapArgs<T> a, T* __re
     }
 }
 
+// One thread's share of interp_kernel: head hv (bit 31: the next sorted node
+// is its same-cell partner) of a staged box, batch entries b0 .. b0+nb-1.
+template <typename T, int D, int W>
+__device__ __forceinline__ void interp_head(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&org)[3],
+                                            uint32_t hv, int b0, int nb, int wk, int nw, int m) {
+    const long long ia = static_cast<long long>(hv & 0x7FFFFFFFu);
+    const bool two = (hv >> 31) != 0;
+    const long long ib = two ? ia + 1 : ia;
+    T taua[3], taub[3];
+    int lb[3] = {0, 0, 0}, lbb[3] = {0, 0, 0};
+    node_setup<T, D>(a.xs, ia, a.g, org, taua, lb, m);
+    node_setup<T, D>(a.xs, ib, a.g, org, taub, lbb, m);   // same cell: lbb = lb
+    const long long da = a.perm[ia], db = a.perm[ib];
+    if constexpr (D >= 2 && sizeof(T) == 4) {
+        // (the closed form here: unrolled polynomial weights in registers
+        // raise this kernel's register count past its occupancy)
+        const int wkc = closed_kind(a.w);
+        if (!a.wfac && nb == 1 && (wkc == WK_SINH || wkc == WK_CSINH || wkc == WK_TABLE)) {
+            C2<T> fa, fb;
+            if (wkc == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
+            else if (wkc == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
+            else interp_pair<T, D, W, WK_TABLE>(a, box, lb, taua, taub, nw, fa, fb);
+            a.fout[static_cast<long long>(b0) * a.N + da] = fa;
+            if (two) a.fout[static_cast<long long>(b0) * a.N + db] = fb;
+            return;
+        }
+    }
+    if constexpr (D >= 2 && sizeof(T) == 8) {
+        if (!a.wfac && nb == 1 && (wk == WK_SINH || wk == WK_CSINH || wk == WK_TABLE)) {
+            a.fout[static_cast<long long>(b0) * a.N + da] = interp_single<T, D, W>(a, box, lb, taua, wk, nw);
+            return;
+        }
+    }
+    // (closed-form weights: see above)
+    interp_node_general<T, D, W>(a, box, slot, lb, taua, closed_kind(a.w), b0, nb, ia, da);
+    if (two) interp_node_general<T, D, W>(a, box, slot, lbb, taub, closed_kind(a.w), b0, nb, ib, db);
+}
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_constant__ CUtensorMap tmap,
                                                              const TapArgs<T> a) {
@@ -1093,41 +1131,100 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
             const int nh = pairs ? static_cast<int>(a.nheads[item]) : wi.count;
             for (int h = threadIdx.x; h < nh; h += blockDim.x) {
                 const uint32_t hv = pairs ? a.heads[wi.start + h] : static_cast<uint32_t>(wi.start + h);
-                const long long ia = static_cast<long long>(hv & 0x7FFFFFFFu);
-                const bool two = (hv >> 31) != 0;
-                const long long ib = two ? ia + 1 : ia;
-                T taua[3], taub[3];
-                int lb[3] = {0, 0, 0}, lbb[3] = {0, 0, 0};
-                node_setup<T, D>(a.xs, ia, a.g, org, taua, lb, m);
-                node_setup<T, D>(a.xs, ib, a.g, org, taub, lbb, m);   // same cell: lbb = lb
-                const long long da = a.perm[ia], db = a.perm[ib];
-                if constexpr (D >= 2 && sizeof(T) == 4) {
-                    // (the closed form here: unrolled polynomial weights in registers
-                    // raise this kernel's register count past its occupancy)
-                    const int wkc = closed_kind(a.w);
-                    if (!a.wfac && nb == 1 && (wkc == WK_SINH || wkc == WK_CSINH || wkc == WK_TABLE)) {
-                        C2<T> fa, fb;
-                        if (wkc == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
-                        else if (wkc == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
-                        else interp_pair<T, D, W, WK_TABLE>(a, box, lb, taua, taub, nw, fa, fb);
-                        a.fout[static_cast<long long>(b0) * a.N + da] = fa;
-                        if (two) a.fout[static_cast<long long>(b0) * a.N + db] = fb;
-                        continue;
-                    }
-                }
-                if constexpr (D >= 2 && sizeof(T) == 8) {
-                    if (!a.wfac && nb == 1 && (wk == WK_SINH || wk == WK_CSINH || wk == WK_TABLE)) {
-                        a.fout[static_cast<long long>(b0) * a.N + da] = interp_single<T, D, W>(a, box, lb, taua, wk, nw);
-                        continue;
-                    }
-                }
-                // (closed-form weights: see above)
-                interp_node_general<T, D, W>(a, box, slot, lb, taua, closed_kind(a.w), b0, nb, ia, da);
-                if (two) interp_node_general<T, D, W>(a, box, slot, lbb, taub, closed_kind(a.w), b0, nb, ib, db);
+                interp_head<T, D, W>(a, box, slot, org, hv, b0, nb, wk, nw, m);
             }
             __syncthreads();
         }
     }
+}
+
+// Interpolation of single-batch d = 3 FP32 plans of the Shannon method (no
+// periodic tiles) with two box buffers per block.  The box of the block's
+// next work item is staged while its warps work on the current one, and
+// each warp takes an item's pair heads 32 at a time, so that a warp that
+// finds no heads left moves on to the next item instead of idling at a
+// block barrier (work items hold a few to several hundred heads).  The last
+// warp to leave an item refills its buffer with the item two ahead.  Every
+// wait is bounded; a block whose wait ran out stops taking work, waits for
+// the copies it issued, and returns (the error flag is set).
+constexpr int kPipeThreads = 512;
+
+template <int W>
+__global__ void __launch_bounds__(kPipeThreads, 1) interp3p_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                   const TapArgs<float> a) {
+    using CT = C2<float>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ int next_head[2];   // heads of the buffer's item taken so far
+    __shared__ int left[2];        // warps still working on the buffer's item
+    __shared__ int issued[2];      // copies issued into the buffer
+    CT* box0 = aligned_box_base<float>(smem);
+    const int box_cells = a.g.box[0] * a.g.box[1] * a.g.box[2];
+    const int slot = box_slot_cells<float>(box_cells);
+    const int nwarps = static_cast<int>(blockDim.x >> 5);
+    const int lane = static_cast<int>(threadIdx.x & 31);
+    const int nw = W ? W : 2 * a.w.m;
+    const int m = nw / 2;
+    const int wk = weight_kind(a.w);
+    auto issue = [&](int buf, int item) {   // one thread
+        int org[3] = {0, 0, 0};
+        tile_origin<3>(a.g, a.work[item].tile, false, org);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&full[buf], static_cast<uint32_t>(box_cells * sizeof(CT)));
+        tma_load_4d(box0 + buf * slot, &tmap, 2 * org[2], org[1], org[0], 0, &full[buf]);
+        issued[buf] += 1;
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_mbar_init();
+        prefetch_tmap(&tmap);
+        for (int b = 0; b < 2; ++b) {
+            next_head[b] = 0;
+            left[b] = nwarps;
+            issued[b] = 0;
+        }
+        if (!a.stall) {   // (stall: nothing arrives, the waits must run out)
+            if (static_cast<int>(blockIdx.x) < a.n_work) issue(0, blockIdx.x);
+            if (static_cast<int>(blockIdx.x + gridDim.x) < a.n_work) issue(1, blockIdx.x + gridDim.x);
+        }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int item = blockIdx.x; item < a.n_work; item += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const bool landed = mbar_wait_bounded(&full[buf], static_cast<uint32_t>((k >> 1) & 1), a.err, a.wait_ns);
+        if (!__all_sync(0xffffffffu, landed)) break;   // one verdict per warp
+        const WorkItem wi = a.work[item];
+        int org[3] = {0, 0, 0};
+        tile_origin<3>(a.g, wi.tile, false, org);
+        const CT* box = box0 + buf * slot;
+        const int nh = static_cast<int>(a.nheads[item]);
+        while (true) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&next_head[buf], 32);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= nh) break;
+            const int h = base + lane;
+            if (h < nh) interp_head<float, 3, W>(a, box, slot, org, a.heads[wi.start + h], 0, 1, wk, nw, m);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();   // this warp's box reads before the count
+            if (atomicSub(&left[buf], 1) == 1) {   // the last warp out: refill
+                __threadfence_block();
+                next_head[buf] = 0;
+                left[buf] = nwarps;
+                const int nxt = item + 2 * static_cast<int>(gridDim.x);
+                if (nxt < a.n_work && !a.stall) issue(buf, nxt);
+            }
+        }
+    }
+    // no copy may still be writing this block's shared memory when it exits
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < 2; ++b)
+            if (issued[b] > 0) mbar_wait_bounded(&full[b], static_cast<uint32_t>((issued[b] - 1) & 1), a.err, a.wait_ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -2042,6 +2139,18 @@ __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_con
 // ---------------------------------------------------------------------------
 // Host launcher for one (precision, dimension): dispatch on m = W/2.
 
+// interp3p_kernel serves single-batch d = 3 FP32 plans of the Shannon method
+// with pair heads (its tiles never wrap) whose boxes are large enough that
+// interp_kernel fits at most two blocks on an SM (above 75 KB: m >= 7 with
+// 8^3 tiles), while two of them still fit in one block.
+inline bool interp3p_applies(const TapArgs<float>& a) {
+    if (a.g.d != 3 || a.heads == nullptr || a.nheads == nullptr || a.batch != 1 || a.w.method != NFFTBL_SHANNON)
+        return false;
+    const long long cells = static_cast<long long>(a.g.box[0]) * a.g.box[1] * a.g.box[2];
+    const long long slot = (cells * 8 + 127) / 128 * 128;
+    return slot > 75 * 1024 && 2 * slot + 128 <= 200 * 1024;
+}
+
 template <typename T, int D, int W>
 nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int kind, size_t smem) {
     void* fn = nullptr;
@@ -2066,6 +2175,16 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         return check_cuda(p, cudaGetLastError(), "factor kernel launch");
     }
     int threads_launch = threads;
+    bool pipe = false;
+    if constexpr (D == 3 && sizeof(T) == 4) {
+        if (kind == TAP_INTERP && interp3p_applies(args)) {
+            pipe = true;
+            fn = reinterpret_cast<void*>(interp3p_kernel<W>);
+            threads_launch = kPipeThreads;
+            const int cells = args.g.box[0] * args.g.box[1] * args.g.box[2];
+            smem = 2 * static_cast<size_t>(box_slot_cells<float>(cells)) * sizeof(C2<T>) + 128;
+        }
+    }
     if constexpr (D == 3 && sizeof(T) == 4 && W >= 4 && W <= 16) {
         if (kind == TAP_SPREAD && spread3c_applies(3, true, W / 2, p->geom.T)) {
             using G = Spread3C<W>;
@@ -2089,7 +2208,10 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
     // (with no work items the spread kernel's CTAs exit at once; the gather still clears the grid)
     if (args.n_work == 0 && kind != TAP_SPREAD) return NFFTBL_OK;
     timing_begin(p, kind == TAP_INTERP ? NFFTBL_K_INTERP : kind == TAP_SPREAD ? NFFTBL_K_SPREAD : NFFTBL_K_GRAD);
-    if (kind == TAP_INTERP)
+    if (kind == TAP_INTERP && pipe) {
+        if constexpr (D == 3 && sizeof(T) == 4)
+            interp3p_kernel<W><<<grid, threads_launch, smem, p->stream>>>(p->tmap, args);
+    } else if (kind == TAP_INTERP)
         interp_kernel<T, D, W><<<grid, kTapThreads, smem, p->stream>>>(p->tmap, args);
     else if (kind == TAP_SPREAD) {
         if constexpr (D == 1) spread1_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);

@@ -27,7 +27,7 @@ def built():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("d,prec", [(2, "f32"), (3, "f64")])
+@pytest.mark.parametrize("d,prec", [(2, "f32"), (3, "f32"), (3, "f64")])
 def test_wait_runs_out_and_plan_recovers(d, prec):
     M, m = {2: (64, 6), 3: (32, 4)}[d]
     N = 3000
