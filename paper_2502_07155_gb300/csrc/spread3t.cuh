@@ -1,0 +1,461 @@
+// d = 3 spreading on the tensor cores (FP32 plans, 8 x 8 x 8 tiles, W = 2m).
+//
+// A work item's box receives, from each of its nodes j, the tensor product
+// g_j w0_j (x) w1_j (x) w2_j (Eq. 4.11 transposed).  Written with the box's
+// dimensions 1 and 2 as rows and dimension 0 (with the real and imaginary
+// part) as columns, the item's box is one matrix product over its nodes:
+//
+//   box[(i1, i2), (i0, c)] = sum_j  A[(i1, i2), j] * B[j, (i0, c)],
+//   A[(i1, i2), j] = w1_j[i1] w2_j[i2],   B[j, (i0, c)] = (g_j w0_j[i0])_c,
+//
+// with every factor zero outside the node's 2m taps.  The rows go in M tiles
+// of 128 (tcgen05 MMA, cta_group::1, kind::tf32), the columns are one N of
+// 2R padded to a multiple of 16, and the nodes are the K dimension, eight
+// per MMA (a "stage").  FP32 accuracy from TF32 operands: each operand is
+// split into its TF32 rounding and the remainder, a = a_hi + a_lo, and the
+// product is a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo is
+// below FP32 rounding).  The tensor core accumulates at most RO stages
+// (3 RO MMAs per output) before the accumulator is added, in FP32 with
+// round-to-nearest, into a box in shared memory: longer chains of
+// accumulations inside the tensor core drift measurably at the dense
+// centre of a spoke workload (a million contributions to a cell).
+//
+// Warp roles (17 warps):
+//  - three producer groups of four warps; group g builds the stages S with
+//    S mod 3 = g into stage buffer g: node parameters, the stage's window
+//    values per box position (node-minor tables, zero outside each node's
+//    taps), then A (hi, lo) into tensor memory with tcgen05.st (warp q of
+//    the group writes lanes 32q .. 32q+31 of every M tile) and B (hi, lo)
+//    into shared memory in the no-swizzle K-major layout;
+//  - one MMA warp: its elected thread issues the stage's 3 x (M tiles) MMAs
+//    and commits them to the buffer's "empty" barrier, and to "dfull" after
+//    the last stage of a segment (at most RO stages of one item);
+//  - one readout group of four warps: after each segment it adds the
+//    accumulator into the shared box, and after an item's last segment it
+//    copies the box to the item's slot of the ordered flush (gather_kernel).
+//
+// Every wait is bounded; after a wait runs out the block sets the error
+// flag and a shared abort word that makes every later wait return at once,
+// so all threads still reach every barrier and the block ends.
+
+template <int W>
+struct Spread3T {
+    static constexpr int T = 8;                          // tile extent, every dimension
+    static constexpr int R = T + W - 1;                  // box extent, dimension 0
+    static constexpr int B1 = T + W - 1;                 // box extent, dimension 1
+    static constexpr int B2 = T + W;                     // box extent, dimension 2 (even origin)
+    static constexpr int ROWS = B1 * B2;                 // GEMM rows
+    static constexpr int NT = (ROWS + 127) / 128;        // M tiles of 128 rows
+    static constexpr int NP = (2 * R + 15) / 16 * 16;    // GEMM columns (i0, re/im), padded
+    static constexpr int KS = 8;                         // nodes per stage (one K step)
+    static constexpr int NG = 3;                         // producer groups = stage buffers
+    static constexpr int RO = 16;                        // stages per accumulator segment
+    static constexpr int COL_A = NT * NP;                // tensor-memory columns: accumulator first
+    static constexpr int A_COLS = 2 * NT * KS;           // A hi and lo of one stage
+    static constexpr int COLS_USED = COL_A + NG * A_COLS;
+    static constexpr int TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
+                                 : COLS_USED <= 256 ? 256 : 512;
+    static constexpr int WARPS = 4 * NG + 4 + 1;         // producers, readout, MMA
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int RD_WARP = 4 * NG;               // first readout warp
+    static constexpr int MMA_WARP = 4 * NG + 4;
+    // stage table (floats, node-minor): g w0 as float2 [R][KS], w1 [B1][KS], w2 [B2][KS]
+    static constexpr int T0 = 0, T1 = 2 * R * KS, T2 = T1 + B1 * KS, TAB = T2 + B2 * KS;
+    static constexpr int NPAR = 12;                      // node parameters: tau[3], s[3], lb[3], g.x, g.y, pad
+    static constexpr int BST = 2 * NP * KS;              // B of one stage (hi, then lo), floats
+    static constexpr int BOX = R * B1 * B2;              // box cells (float2)
+    // shared memory (bytes)
+    static constexpr size_t OFF_TAB = static_cast<size_t>(BOX) * 8;
+    static constexpr size_t OFF_PAR = OFF_TAB + static_cast<size_t>(NG) * 2 * TAB * 4;
+    static constexpr size_t OFF_B = (OFF_PAR + static_cast<size_t>(NG) * 2 * KS * NPAR * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_BAR = (OFF_B + static_cast<size_t>(NG) * BST * 4 + 127) / 128 * 128;
+    static constexpr size_t BYTES = OFF_BAR + 8 * (2 * NG + 3) + 16;
+    // at least 116 KB: one block per SM, the tensor-memory allocation never waits on another block
+    static constexpr size_t SMEM = BYTES > 116 * 1024 ? BYTES : 116 * 1024;
+    static_assert(COLS_USED <= 512, "tensor memory holds 512 columns");
+    static_assert(NP <= 256 && NP % 16 == 0, "MMA N for M = 128");
+    static_assert(NT * 128 >= ROWS, "M tiles cover the rows");
+    static_assert(BOX % 2 == 0 && (TAB * 4) % 16 == 0 && (T1 * 4) % 16 == 0 && (T2 * 4) % 16 == 0, "alignment");
+};
+
+// ---- tcgen05 / tensor-memory helpers (sm_100 family PTX) -------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Two consecutive 32-bit columns of this thread's lane.
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float v0, float v1) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(__float_as_uint(v0)),
+                 "r"(__float_as_uint(v1))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Four consecutive 32-bit columns of this thread's lane, waited for in the
+// same statement (no use of the registers can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(taddr)
+        : "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
+}
+
+// D (tensor memory) (+)= A (tensor memory) * B (shared memory, descriptor).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// The barrier receives one arrival when every MMA this thread issued so far
+// has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ float tf32_round(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, no negation or sparsity, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, no swizzle: core matrices of 8 rows x 16
+// bytes stored contiguously; lbo = byte step between core matrices along K,
+// sbo = byte step between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_noswz(const void* p, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = static_cast<uint64_t>((smem_addr(p) >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;   // descriptor version of the sm_100 family
+    return d;
+}
+
+// Bounded wait that also gives up at once when another thread of the block
+// has already given up (abort word set).
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
+                                              unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > limit_ns) {
+            *abort = 1;
+            atomicOr(err, DEVERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+// Sixteen consecutive 32-bit columns of this thread's lane (waited for in
+// the same statement).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// One tap weight of a closed-form kind (s: the kind's sine of the node).
+__device__ __forceinline__ float s3t_weight(int wk, float tau, float s, int a, int m, const WinParams<float>& wp) {
+    if (wk == WK_SINH) return fast_weight<float, WK_SINH>(tau, s, a, m, wp);
+    if (wk == WK_TABLE) return fast_weight<float, WK_TABLE>(tau, s, a, m, wp);
+    if (wk == WK_CSINH) return fast_weight<float, WK_CSINH>(tau, s, a, m, wp);
+    return fast_weight<float, WK_POLY>(tau, s, a, m, wp);
+}
+
+template <int W>
+__global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const TapArgs<float> a) {
+    using G = Spread3T<W>;
+    constexpr int m = W / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* s_box = reinterpret_cast<float2*>(smem);
+    float* s_tab = reinterpret_cast<float*>(smem + G::OFF_TAB);
+    float* s_par = reinterpret_cast<float*>(smem + G::OFF_PAR);
+    float* s_b = reinterpret_cast<float*>(smem + G::OFF_B);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);   // [NG], 128 arrivals
+    uint64_t* empty = full + G::NG;                                     // [NG], one commit
+    uint64_t* dfull = empty + G::NG;                                    // segment accumulated (commit)
+    uint64_t* dempty = dfull + 1;                                       // segment read (128 arrivals)
+    uint64_t* fin = dempty + 1;                                         // final drain (commit)
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wk = weight_kind(a.w);
+    const bool periodic = a.w.method == NFFTBL_CLASSIC;
+    constexpr uint32_t kIdesc = idesc_tf32(128, G::NP);
+
+    if (tid == 0) {
+        for (int b = 0; b < G::NG; ++b) {
+            mbar_init(&full[b], 128);
+            mbar_init(&empty[b], 1);
+        }
+        mbar_init(dfull, 1);
+        mbar_init(dempty, 128);
+        mbar_init(fin, 1);
+        *s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == G::MMA_WARP) {   // the MMA warp owns the tensor memory
+        tmem_alloc(s_tmem, G::TCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *s_tmem;
+
+    if (warp == G::MMA_WARP) {
+        // ---------------- MMA warp: one elected thread issues every MMA
+        if (lane == 0) {
+            bool issued = false;
+            long long S = 0;   // stage counter
+            int seg = 0;       // segment counter
+            for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+                const int ns = max(1, (a.work[item].count + G::KS - 1) / G::KS);
+                for (int s = 0; s < ns; ++s, ++S) {
+                    const int b = static_cast<int>(S % G::NG);
+                    const bool first = (s % G::RO) == 0, last = (s % G::RO) == G::RO - 1 || s == ns - 1;
+                    bool ok = wait_or_abort(&full[b], static_cast<uint32_t>((S / G::NG) & 1), s_abort, a.err, a.wait_ns);
+                    if (ok && first && seg > 0)
+                        ok = wait_or_abort(dempty, static_cast<uint32_t>((seg - 1) & 1), s_abort, a.err, a.wait_ns);
+                    if (ok) {
+                        tc_fence_after();
+                        const float* bh = s_b + static_cast<size_t>(b) * G::BST;
+                        const uint64_t dh = smem_desc_noswz(bh, 128, 256);
+                        const uint64_t dl = smem_desc_noswz(bh + G::NP * G::KS, 128, 256);
+#pragma unroll 1
+                        for (int t = 0; t < G::NT; ++t) {
+                            const uint32_t d = tbase + static_cast<uint32_t>(t * G::NP);
+                            const uint32_t ah = tbase + static_cast<uint32_t>(G::COL_A + b * G::A_COLS + t * G::KS);
+                            const uint32_t al = ah + static_cast<uint32_t>(G::NT * G::KS);
+                            mma_tf32_ts(d, ah, dh, kIdesc, first ? 0u : 1u);
+                            mma_tf32_ts(d, ah, dl, kIdesc, 1u);
+                            mma_tf32_ts(d, al, dh, kIdesc, 1u);
+                        }
+                        issued = true;
+                        mma_commit(&empty[b]);
+                        if (last) mma_commit(dfull);
+                    }
+                    if (last) ++seg;
+                }
+            }
+            if (issued) {   // nothing may still run on the tensor memory when it is freed
+                mma_commit(fin);
+                mbar_wait_bounded(fin, 0, a.err, a.wait_ns);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= G::RD_WARP) {
+        // ---------------- readout group: accumulator segments into the shared box
+        const int q = warp & 3, rt = tid - 32 * G::RD_WARP;   // lane quarter, thread of the group
+        const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
+        int seg = 0;
+        for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+            const int ns = max(1, (a.work[item].count + G::KS - 1) / G::KS);
+            const int nseg = (ns + G::RO - 1) / G::RO;
+            for (int sg = 0; sg < nseg; ++sg, ++seg) {
+                wait_or_abort(dfull, static_cast<uint32_t>(seg & 1), s_abort, a.err, a.wait_ns);
+                tc_fence_after();
+#pragma unroll 1
+                for (int t = 0; t < G::NT; ++t) {
+                    const int r = 128 * t + 32 * q + lane;
+                    const int i1 = r / G::B2, i2 = r - (r / G::B2) * G::B2;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < G::NP; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(lane_base + static_cast<uint32_t>(t * G::NP + c0), v);
+                        if (r < G::ROWS) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int i0 = c0 / 2 + u;
+                                if (i0 < G::R) {
+                                    float2* cell = s_box + (i0 * G::B1 + i1) * G::B2 + i2;
+                                    if (sg == 0) {
+                                        *cell = make_float2(v[2 * u], v[2 * u + 1]);
+                                    } else {
+                                        const float2 o = *cell;
+                                        *cell = make_float2(o.x + v[2 * u], o.y + v[2 * u + 1]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(dempty);
+            }
+            // the item's box into its slot of the ordered flush
+            named_sync(1 + G::NG, 128);
+            const float4* src = reinterpret_cast<const float4*>(s_box);
+            float4* dst = reinterpret_cast<float4*>(a.part + static_cast<long long>(item) * G::BOX);
+            for (int idx = rt; idx < G::BOX / 2; idx += 128) dst[idx] = src[idx];
+            named_sync(1 + G::NG, 128);
+        }
+    } else {
+        // ---------------- producer group grp: stages S with S mod NG = grp
+        const int grp = warp >> 2, q = warp & 3, gt = tid - 128 * grp;   // group, lane quarter, thread of the group
+        const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
+        int tb = 0;
+        long long S0 = 0;   // first stage of the item
+        for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
+            const WorkItem wi = a.work[item];
+            const int ns = max(1, (wi.count + G::KS - 1) / G::KS);
+            int org[3] = {0, 0, 0};
+            tile_origin<3>(a.g, wi.tile, periodic, org);
+            for (int s = static_cast<int>(((grp - S0) % G::NG + G::NG) % G::NG); s < ns; s += G::NG) {
+                const long long S = S0 + s;
+                float* par = s_par + static_cast<size_t>(grp * 2 + tb) * G::KS * G::NPAR;
+                float* tab = s_tab + static_cast<size_t>(grp * 2 + tb) * G::TAB;
+                // node parameters of the stage's nodes (lb = -1000 marks no node)
+                if (gt < G::KS) {
+                    const int c = s * G::KS + gt;
+                    float* pp = par + gt * G::NPAR;
+                    if (c < wi.count) {
+                        const long long i = static_cast<long long>(wi.start) + c;
+                        float tau[3];
+                        int lb[3];
+                        node_setup<float, 3>(a.xs, i, a.g, org, tau, lb, m);
+                        const float2 gv = a.fin[a.perm[i]];
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const float sn = (wk == WK_SINH)    ? kind_sin<float, WK_SINH>(tau[t], a.w)
+                                             : (wk == WK_TABLE) ? kind_sin<float, WK_TABLE>(tau[t], a.w)
+                                                                : 0.0f;
+                            pp[t] = tau[t];
+                            pp[3 + t] = sn;
+                            pp[6 + t] = __int_as_float(lb[t]);
+                        }
+                        pp[9] = gv.x;
+                        pp[10] = gv.y;
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            pp[t] = 0.0f;
+                            pp[3 + t] = 0.0f;
+                            pp[6 + t] = __int_as_float(-1000);
+                        }
+                        pp[9] = pp[10] = 0.0f;
+                    }
+                }
+                named_sync(1 + grp, 128);
+                // window values per box position (zero outside each node's taps)
+                constexpr int E = G::KS * (G::R + G::B1 + G::B2);
+                for (int e = gt; e < E; e += 128) {
+                    const int k = e & (G::KS - 1), pe = e / G::KS;   // node, position entry
+                    const int t = pe < G::R ? 0 : pe < G::R + G::B1 ? 1 : 2;
+                    const int pos = pe - (t == 0 ? 0 : t == 1 ? G::R : G::R + G::B1);
+                    const float* pp = par + k * G::NPAR;
+                    const int tap = pos - __float_as_int(pp[6 + t]);
+                    float w = 0.0f;
+                    if (tap >= 0 && tap < W) w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
+                    if (t == 0)
+                        reinterpret_cast<float2*>(tab + G::T0)[pos * G::KS + k] = make_float2(pp[9] * w, pp[10] * w);
+                    else
+                        tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
+                }
+                named_sync(1 + grp, 128);
+                if (S >= G::NG)
+                    wait_or_abort(&empty[grp], static_cast<uint32_t>(((S / G::NG) - 1) & 1), s_abort, a.err,
+                                  a.wait_ns);
+                tc_fence_after();
+                // A = w1[i1] w2[i2] for the stage's eight nodes, hi and lo
+                const uint32_t col = static_cast<uint32_t>(G::COL_A + grp * G::A_COLS);
+#pragma unroll
+                for (int t = 0; t < G::NT; ++t) {
+                    const int r = 128 * t + 32 * q + lane;
+                    const bool in = r < G::ROWS;
+                    const int i1 = in ? r / G::B2 : 0, i2 = in ? r - (r / G::B2) * G::B2 : 0;
+                    const float4* p1 = reinterpret_cast<const float4*>(tab + G::T1 + i1 * G::KS);
+                    const float4* p2 = reinterpret_cast<const float4*>(tab + G::T2 + i2 * G::KS);
+                    const float4 x0 = p1[0], x1 = p1[1], y0 = p2[0], y1 = p2[1];
+                    float hi[8], lo[8];
+                    const float av[8] = {x0.x * y0.x, x0.y * y0.y, x0.z * y0.z, x0.w * y0.w,
+                                         x1.x * y1.x, x1.y * y1.y, x1.z * y1.z, x1.w * y1.w};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float v = in ? av[u] : 0.0f;
+                        hi[u] = tf32_round(v);
+                        lo[u] = v - hi[u];
+                    }
+                    tmem_st8(lane_base + col + static_cast<uint32_t>(t * G::KS), hi);
+                    tmem_st8(lane_base + col + static_cast<uint32_t>((G::NT + t) * G::KS), lo);
+                }
+                // B = (g w0)[(i0, c)] of the stage's eight nodes, K-major core matrices of 8 x 4
+                float* bh = s_b + static_cast<size_t>(grp) * G::BST;
+                for (int idx = gt; idx < G::NP * G::KS; idx += 128) {
+                    const int n = idx / G::KS, kk = idx - n * G::KS;
+                    const float v = n < 2 * G::R ? tab[G::T0 + (n >> 1) * 2 * G::KS + 2 * kk + (n & 1)] : 0.0f;
+                    const float h = tf32_round(v);
+                    const int off = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
+                    bh[off] = h;
+                    bh[G::NP * G::KS + off] = v - h;
+                }
+                tmem_wait_st();
+                fence_async_shared();
+                tc_fence_before();
+                mbar_arrive(&full[grp]);
+                tb ^= 1;
+            }
+            S0 += ns;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == G::MMA_WARP) tmem_dealloc(tbase, G::TCOLS);
+}

@@ -1835,6 +1835,8 @@ __global__ void __launch_bounds__(Spread3C<W>::THREADS, 1) spread3c_kernel(const
     }
 }
 
+#include "spread3t.cuh"
+
 // d = 1 spreading.  Nodes are staged `sub` at a time (weights and the
 // pre-scaled inputs in shared memory); runs of nodes in one cell share their
 // 2m taps.  A warp takes a run: lane l owns tap c = l mod 2m and row group
@@ -2139,6 +2141,15 @@ __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_con
 // ---------------------------------------------------------------------------
 // Host launcher for one (precision, dimension): dispatch on m = W/2.
 
+// spread3t_kernel serves single-batch FP32 plans without stored factors whose
+// window has a per-tap closed form there (sinh, tabulated Shannon window, or
+// fitted polynomials); the geometry test is the column-owner kernel's.
+inline bool spread3t_applies(const TapArgs<float>& a) {
+    if (a.batch != 1 || a.wfac != nullptr) return false;
+    if (a.w.poly) return true;
+    return a.w.window == NFFTBL_WIN_SINH || (a.w.window == NFFTBL_WIN_TABLE && a.w.method == NFFTBL_SHANNON);
+}
+
 // interp3p_kernel serves single-batch d = 3 FP32 plans of the Shannon method
 // with pair heads (its tiles never wrap) whose boxes are large enough that
 // interp_kernel fits at most two blocks on an SM (above 75 KB: m >= 7 with
@@ -2175,7 +2186,7 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         return check_cuda(p, cudaGetLastError(), "factor kernel launch");
     }
     int threads_launch = threads;
-    bool pipe = false;
+    bool pipe = false, tensor = false;
     if constexpr (D == 3 && sizeof(T) == 4) {
         if (kind == TAP_INTERP && interp3p_applies(args)) {
             pipe = true;
@@ -2193,6 +2204,12 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
             fn = reinterpret_cast<void*>(spread3c_kernel<W>);
             threads_launch = G::THREADS;
             smem = G::SMEM;
+            if (spread3t_applies(args)) {   // the tensor-core form
+                tensor = true;
+                fn = reinterpret_cast<void*>(spread3t_kernel<W>);
+                threads_launch = Spread3T<W>::THREADS;
+                smem = Spread3T<W>::SMEM;
+            }
         }
     }
     nfftbl_status st = check_cuda(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2217,8 +2234,12 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         if constexpr (D == 1) spread1_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
         else if constexpr (D == 2) spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
         else if (threads_launch != threads) {
-            if constexpr (sizeof(T) == 4 && W >= 4 && W <= 16)
-                spread3c_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
+            if constexpr (sizeof(T) == 4 && W >= 4 && W <= 16) {
+                if (tensor)
+                    spread3t_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
+                else
+                    spread3c_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
+            }
         } else spread3_kernel<T, W><<<grid, threads, smem, p->stream>>>(args);
     }
     else
