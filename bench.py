@@ -65,12 +65,13 @@ CONFIGS = {
     "d1_M256_m8_N1024": (1, 256, 8, 1024, 1, "uniform"),
     # smaller spoke case for profiler captures (same density profile, 1/8 of the nodes)
     "d3_M128_m6_N2^20_spokes": (3, 128, 6, 1 << 20, 1, "spokes"),
+    "d3_M128_m8_N2^20_spokes": (3, 128, 8, 1 << 20, 1, "spokes"),
 }
 DEFAULT_CONFIG = "d2_M256_m8_N2^20"
 # FP32 flavour of the timed plan: the d = 3 workload is specified with
 # compensated accumulation of the tap sums ("f32c"), the others plain FP32.
 PRECISION = {"d3_M128_m6_N2^23_spokes": "f32c", "d3_M128_m8_N2^23_spokes": "f32c",
-             "d3_M128_m6_N2^20_spokes": "f32c"}
+             "d3_M128_m6_N2^20_spokes": "f32c", "d3_M128_m8_N2^20_spokes": "f32c"}
 
 # GB300 unit counts at the maximum SM clock (2070 MHz): 152 SMs; 128 FP32
 # FMA lanes per SM; the special-function unit issues 16 lanes per SM per clock
@@ -116,6 +117,39 @@ def short_sum_roofline(d, m, N, B, M, seconds):
     out["sfu_slots_per_launch"] = slots
     out["hbm_bytes_per_launch"] = hbm_bytes
     return out
+
+
+# Nominal dense tensor rates of GB300, TF32 : BF16 (1.1 : 2.25 PFLOP/s); the
+# TF32 peak is the measured BF16 GEMM rate times this ratio.
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tensor_spread_roofline(x, M, m, seconds):
+    """Tensor-pipe view of the d = 3 FP32 spreading launch (spread3t_kernel):
+    the MMA flops it issues, per work item ceil(nodes / 8) stages of
+    (M tiles) x 3 TF32 MMAs of 128 x NP x 8, with the binning's items (8^3
+    tiles of L = 2M, at most 1024 nodes each), against the measured BF16
+    peak times the nominal TF32/BF16 ratio.  These flops include the
+    padding of the box to whole M tiles and the split-operand products, so
+    the fraction says how busy the tensor pipe is, not how close the
+    algorithm is to its bound (that is the FP32 roofline beside it)."""
+    L, T, K = 2 * M, 8, 1024
+    u = (np.float32(L) * x.astype(np.float32)).astype(np.float32)
+    cell = np.floor(u).astype(np.int64) + L // 2
+    tile = ((cell[:, 0] // T) * (L // T) + cell[:, 1] // T) * (L // T) + cell[:, 2] // T
+    counts = np.bincount(tile)
+    counts = counts[counts > 0]
+    stages = int(((counts // K) * (K // 8)).sum() + ((counts % K + 7) // 8).sum())
+    W = 2 * m
+    R, B2 = T + W - 1, T + W
+    NT = (R * B2 + 127) // 128
+    NP = (2 * R + 15) // 16 * 16
+    flops = float(stages) * NT * 3 * 128 * NP * 8 * 2
+    peak = float(measured_peaks().get("bf16_tflops", 1900.0)) * TF32_PER_BF16
+    achieved = flops / seconds / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "mma_flops_per_launch": flops, "stages": stages,
+            "peak_note": "measured bf16 GEMM burst x 1.1/2.25 (nominal TF32 : BF16), kind::tf32 MMAs"}
 
 
 def aggregate_over_ranks(t_step_ms, units_per_rank, world, device=None):
@@ -682,6 +716,9 @@ def measure(nb, cfg, args, dev, flush, full):
     o_ms, o_n = ktimes[other]
     res["roofline_other"] = dict(short_sum_roofline(d, m, N, B, M, o_ms / max(o_n, 1) * 1e-3), kernel=other,
                                  traffic=traffic_from_profiles(cfg, other))
+    if d == 3 and B == 1 and 2 <= m <= 8 and PRECISION.get(cfg, "f32") in ("f32", "f32c"):
+        sp = res["roofline"] if dom == "spread" else res["roofline_other"]
+        sp["tensor"] = tensor_spread_roofline(x, M, m, ktimes["spread"][0] / max(ktimes["spread"][1], 1) * 1e-3)
 
     # plain FP64 GPU path on the same inputs, timed both ways
     plan64 = nb.Plan(d, M, 2.0, m, precision="f64", batch=B)

@@ -460,6 +460,11 @@ nfftbl_status bin_nodes(nfftbl_plan_s* p, long long N, const void* x_dev) {
         p->N = -1;
         return st;
     }
+    // FP32 d = 3: the spreading's input gathered into sorted node order
+    if (d == 3 && !dbl && p->batch == 1 && (st = ensure_buf(p, p->fsorted, Nb * 8)) != NFFTBL_OK) {
+        p->N = -1;
+        return st;
+    }
     // same-cell pairs of the interpolation (heads per item)
     if ((st = ensure_buf(p, p->heads, Nb * 4)) != NFFTBL_OK || (st = ensure_buf(p, p->nheads,
                                                                                 std::max<uint32_t>(host_total, 1) * 4)) != NFFTBL_OK) {

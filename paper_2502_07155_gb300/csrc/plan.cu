@@ -153,6 +153,7 @@ TapArgs<T> make_tap_args(nfftbl_plan_s* p) {
     a.work = static_cast<const WorkItem*>(p->work.p);
     a.heads = static_cast<const uint32_t*>(p->heads.p);
     a.nheads = static_cast<const uint32_t*>(p->nheads.p);
+    a.fsorted = static_cast<C2<T>*>(p->fsorted.p);
     a.n_work = static_cast<int>(p->n_work);
     a.N = p->N;
     a.grid = static_cast<C2<T>*>(p->grid.p);
@@ -272,6 +273,7 @@ void destroy_plan(nfftbl_plan_s* p) {
     free_buf(p->tile_items);
     free_buf(p->part);
     free_buf(p->heads);
+    free_buf(p->fsorted);
     free_buf(p->nheads);
     free_buf(p->counters);
     free_buf(p->lw_f);

@@ -82,6 +82,7 @@ struct TapArgs {
     T wbound;                  // bound on prod_t |window factor| (1 for sinh / cKB)
     int spread_warps;          // warps per block of the d = 3 spread kernel
     const T* wfac;             // stored window factors (sorted node i: row i of wstride), or null
+    C2<T>* fsorted;            // FP32 d = 3 spreading: fin in sorted node order (N complex), or null
     int wstride;               // row length of wfac: d * 2m rounded up to a multiple of 4
 };
 
@@ -288,6 +289,7 @@ struct nfftbl_plan_s {
     nfftbl::DeviceBuf tile_items;         // n_tiles + 1: first work item per tile
     nfftbl::DeviceBuf part;               // spread boxes, one slot per (item, batch entry)
     nfftbl::DeviceBuf heads, nheads;      // same-cell pair heads per work item (interpolation)
+    nfftbl::DeviceBuf fsorted;            // FP32 d = 3: the adjoint input in sorted node order (N complex)
     nfftbl::DeviceBuf counters;           // small device scratch (ints)
     long long n_tiles = 0;
     long long n_work = 0;

@@ -350,112 +350,157 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
         // ---------------- producer group grp: stages S with S mod NG = grp
         const int grp = warp >> 2, q = warp & 3, gt = tid - 128 * grp;   // group, lane quarter, thread of the group
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
-        int tb = 0;
-        long long S0 = 0;   // first stage of the item
-        for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
-            const WorkItem wi = a.work[item];
-            const int ns = max(1, (wi.count + G::KS - 1) / G::KS);
-            int org[3] = {0, 0, 0};
-            tile_origin<3>(a.g, wi.tile, periodic, org);
-            for (int s = static_cast<int>(((grp - S0) % G::NG + G::NG) % G::NG); s < ns; s += G::NG) {
-                const long long S = S0 + s;
-                float* par = s_par + static_cast<size_t>(grp * 2 + tb) * G::KS * G::NPAR;
-                float* tab = s_tab + static_cast<size_t>(grp * 2 + tb) * G::TAB;
-                // node parameters of the stage's nodes (lb = -1000 marks no node)
-                if (gt < G::KS) {
-                    const int c = s * G::KS + gt;
-                    float* pp = par + gt * G::NPAR;
-                    if (c < wi.count) {
-                        const long long i = static_cast<long long>(wi.start) + c;
-                        float tau[3];
-                        int lb[3];
-                        node_setup<float, 3>(a.xs, i, a.g, org, tau, lb, m);
-                        const float2 gv = a.fin[a.perm[i]];
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) {
-                            const float sn = (wk == WK_SINH)    ? kind_sin<float, WK_SINH>(tau[t], a.w)
-                                             : (wk == WK_TABLE) ? kind_sin<float, WK_TABLE>(tau[t], a.w)
-                                                                : 0.0f;
-                            pp[t] = tau[t];
-                            pp[3 + t] = sn;
-                            pp[6 + t] = __int_as_float(lb[t]);
-                        }
-                        pp[9] = gv.x;
-                        pp[10] = gv.y;
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < 3; ++t) {
-                            pp[t] = 0.0f;
-                            pp[3 + t] = 0.0f;
-                            pp[6 + t] = __int_as_float(-1000);
-                        }
-                        pp[9] = pp[10] = 0.0f;
-                    }
+        // the group's stages in order; thread gt < 3 KS holds the coordinate (node
+        // gt / 3, dimension gt mod 3) and, for dimension 0, the input value of the
+        // next stage, loaded one stage ahead
+        struct StageRef {
+            int item, s, ns, start, count, org;   // org: this thread's dimension's box origin
+            long long S0;                          // first global stage of the item
+        };
+        const int pk = gt / 3, pt = gt - 3 * (gt / 3);
+        auto first_of = [&](int item, long long S0, StageRef& r) {
+            while (item < a.n_work) {
+                const WorkItem wi = a.work[item];
+                const int ns = max(1, (wi.count + G::KS - 1) / G::KS);
+                const int s0 = static_cast<int>(((grp - S0) % G::NG + G::NG) % G::NG);
+                if (s0 < ns) {
+                    int org[3] = {0, 0, 0};
+                    tile_origin<3>(a.g, wi.tile, periodic, org);
+                    r = {item, s0, ns, static_cast<int>(wi.start), wi.count, pt == 0 ? org[0] : pt == 1 ? org[1] : org[2],
+                         S0};
+                    return;
                 }
-                named_sync(1 + grp, 128);
-                // window values per box position (zero outside each node's taps)
-                constexpr int E = G::KS * (G::R + G::B1 + G::B2);
-                for (int e = gt; e < E; e += 128) {
-                    const int k = e & (G::KS - 1), pe = e / G::KS;   // node, position entry
-                    const int t = pe < G::R ? 0 : pe < G::R + G::B1 ? 1 : 2;
-                    const int pos = pe - (t == 0 ? 0 : t == 1 ? G::R : G::R + G::B1);
-                    const float* pp = par + k * G::NPAR;
-                    const int tap = pos - __float_as_int(pp[6 + t]);
-                    float w = 0.0f;
-                    if (tap >= 0 && tap < W) w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
-                    if (t == 0)
-                        reinterpret_cast<float2*>(tab + G::T0)[pos * G::KS + k] = make_float2(pp[9] * w, pp[10] * w);
-                    else
-                        tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
-                }
-                named_sync(1 + grp, 128);
-                if (S >= G::NG)
-                    wait_or_abort(&empty[grp], static_cast<uint32_t>(((S / G::NG) - 1) & 1), s_abort, a.err,
-                                  a.wait_ns);
-                tc_fence_after();
-                // A = w1[i1] w2[i2] for the stage's eight nodes, hi and lo
-                const uint32_t col = static_cast<uint32_t>(G::COL_A + grp * G::A_COLS);
-#pragma unroll
-                for (int t = 0; t < G::NT; ++t) {
-                    const int r = 128 * t + 32 * q + lane;
-                    const bool in = r < G::ROWS;
-                    const int i1 = in ? r / G::B2 : 0, i2 = in ? r - (r / G::B2) * G::B2 : 0;
-                    const float4* p1 = reinterpret_cast<const float4*>(tab + G::T1 + i1 * G::KS);
-                    const float4* p2 = reinterpret_cast<const float4*>(tab + G::T2 + i2 * G::KS);
-                    const float4 x0 = p1[0], x1 = p1[1], y0 = p2[0], y1 = p2[1];
-                    float hi[8], lo[8];
-                    const float av[8] = {x0.x * y0.x, x0.y * y0.y, x0.z * y0.z, x0.w * y0.w,
-                                         x1.x * y1.x, x1.y * y1.y, x1.z * y1.z, x1.w * y1.w};
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const float v = in ? av[u] : 0.0f;
-                        hi[u] = tf32_round(v);
-                        lo[u] = v - hi[u];
-                    }
-                    tmem_st8(lane_base + col + static_cast<uint32_t>(t * G::KS), hi);
-                    tmem_st8(lane_base + col + static_cast<uint32_t>((G::NT + t) * G::KS), lo);
-                }
-                // B = (g w0)[(i0, c)] of the stage's eight nodes, K-major core matrices of 8 x 4
-                float* bh = s_b + static_cast<size_t>(grp) * G::BST;
-                for (int idx = gt; idx < G::NP * G::KS; idx += 128) {
-                    const int n = idx / G::KS, kk = idx - n * G::KS;
-                    const float v = n < 2 * G::R ? tab[G::T0 + (n >> 1) * 2 * G::KS + 2 * kk + (n & 1)] : 0.0f;
-                    const float h = tf32_round(v);
-                    const int off = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
-                    bh[off] = h;
-                    bh[G::NP * G::KS + off] = v - h;
-                }
-                tmem_wait_st();
-                fence_async_shared();
-                tc_fence_before();
-                mbar_arrive(&full[grp]);
-                tb ^= 1;
+                S0 += ns;
+                item += gridDim.x;
             }
-            S0 += ns;
+            r = {a.n_work, 0, 0, 0, 0, 0, S0};
+        };
+        auto next_of = [&](const StageRef& c, StageRef& r) {
+            if (c.s + G::NG < c.ns) {
+                r = c;
+                r.s += G::NG;
+            } else {
+                first_of(c.item + gridDim.x, c.S0 + c.ns, r);
+            }
+        };
+        float px = 0.0f;
+        float2 pg = make_float2(0.0f, 0.0f);
+        auto prefetch = [&](const StageRef& r) {
+            const int c = r.s * G::KS + pk;
+            if (gt < 3 * G::KS && r.item < a.n_work && c < r.count) {
+                const long long i = static_cast<long long>(r.start) + c;
+                px = a.xs[i * 3 + pt];
+                if (pt == 0) pg = a.fsorted[i];
+            }
+        };
+        int tb = 0;
+        StageRef cur;
+        first_of(blockIdx.x, 0, cur);
+        prefetch(cur);
+        while (cur.item < a.n_work) {
+            const long long S = cur.S0 + cur.s;
+            float* par = s_par + static_cast<size_t>(grp * 2 + tb) * G::KS * G::NPAR;
+            float* tab = s_tab + static_cast<size_t>(grp * 2 + tb) * G::TAB;
+            // node parameters (lb = -1000 marks no node), from the prefetched values
+            if (gt < 3 * G::KS) {
+                float* pp = par + pk * G::NPAR;
+                if (cur.s * G::KS + pk < cur.count) {
+                    const int Lt = pt == 0 ? a.g.L[0] : pt == 1 ? a.g.L[1] : a.g.L[2];
+                    const float u = mul_rn(static_cast<float>(Lt), px);
+                    const float fl = FM<float>::flr(u);
+                    const float tau = u - fl;
+                    const int lb = static_cast<int>(fl) + Lt / 2 - (m - 1) - cur.org;
+                    pp[pt] = tau;
+                    pp[3 + pt] = (wk == WK_SINH)    ? kind_sin<float, WK_SINH>(tau, a.w)
+                                 : (wk == WK_TABLE) ? kind_sin<float, WK_TABLE>(tau, a.w)
+                                                    : 0.0f;
+                    pp[6 + pt] = __int_as_float(lb);
+                    if (pt == 0) {
+                        pp[9] = pg.x;
+                        pp[10] = pg.y;
+                    }
+                } else {
+                    pp[pt] = 0.0f;
+                    pp[3 + pt] = 0.0f;
+                    pp[6 + pt] = __int_as_float(-1000);
+                    if (pt == 0) pp[9] = pp[10] = 0.0f;
+                }
+            }
+            named_sync(1 + grp, 128);
+            // window values per box position (zero outside each node's taps)
+            constexpr int E = G::KS * (G::R + G::B1 + G::B2);
+            for (int e = gt; e < E; e += 128) {
+                const int k = e & (G::KS - 1), pe = e / G::KS;   // node, position entry
+                const int t = pe < G::R ? 0 : pe < G::R + G::B1 ? 1 : 2;
+                const int pos = pe - (t == 0 ? 0 : t == 1 ? G::R : G::R + G::B1);
+                const float* pp = par + k * G::NPAR;
+                const int tap = pos - __float_as_int(pp[6 + t]);
+                float w = 0.0f;
+                if (tap >= 0 && tap < W) w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
+                if (t == 0)
+                    reinterpret_cast<float2*>(tab + G::T0)[pos * G::KS + k] = make_float2(pp[9] * w, pp[10] * w);
+                else
+                    tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
+            }
+            named_sync(1 + grp, 128);
+            StageRef nxt;
+            next_of(cur, nxt);
+            prefetch(nxt);   // (consumed at the next stage: the loads overlap this stage's build)
+            if (S >= G::NG)
+                wait_or_abort(&empty[grp], static_cast<uint32_t>(((S / G::NG) - 1) & 1), s_abort, a.err, a.wait_ns);
+            tc_fence_after();
+            // A = w1[i1] w2[i2] for the stage's eight nodes, hi and lo
+            const uint32_t col = static_cast<uint32_t>(G::COL_A + grp * G::A_COLS);
+#pragma unroll
+            for (int t = 0; t < G::NT; ++t) {
+                const int r = 128 * t + 32 * q + lane;
+                const bool in = r < G::ROWS;
+                const int i1 = in ? r / G::B2 : 0, i2 = in ? r - (r / G::B2) * G::B2 : 0;
+                const float4* p1 = reinterpret_cast<const float4*>(tab + G::T1 + i1 * G::KS);
+                const float4* p2 = reinterpret_cast<const float4*>(tab + G::T2 + i2 * G::KS);
+                const float4 x0 = p1[0], x1 = p1[1], y0 = p2[0], y1 = p2[1];
+                float hi[8], lo[8];
+                const float av[8] = {x0.x * y0.x, x0.y * y0.y, x0.z * y0.z, x0.w * y0.w,
+                                     x1.x * y1.x, x1.y * y1.y, x1.z * y1.z, x1.w * y1.w};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float v = in ? av[u] : 0.0f;
+                    hi[u] = tf32_round(v);
+                    lo[u] = v - hi[u];
+                }
+                tmem_st8(lane_base + col + static_cast<uint32_t>(t * G::KS), hi);
+                tmem_st8(lane_base + col + static_cast<uint32_t>((G::NT + t) * G::KS), lo);
+            }
+            // B = (g w0)[(i0, c)] of the stage's eight nodes, K-major core matrices of 8 x 4
+            float* bh = s_b + static_cast<size_t>(grp) * G::BST;
+            for (int idx = gt; idx < G::NP * G::KS; idx += 128) {
+                const int n = idx / G::KS, kk = idx - n * G::KS;
+                const float v = n < 2 * G::R ? tab[G::T0 + (n >> 1) * 2 * G::KS + 2 * kk + (n & 1)] : 0.0f;
+                const float h = tf32_round(v);
+                const int off = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
+                bh[off] = h;
+                bh[G::NP * G::KS + off] = v - h;
+            }
+            tmem_wait_st();
+            fence_async_shared();
+            tc_fence_before();
+            mbar_arrive(&full[grp]);
+            tb ^= 1;
+            cur = nxt;
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == G::MMA_WARP) tmem_dealloc(tbase, G::TCOLS);
+}
+
+// The spreading's input in sorted node order: out[i] = fin[perm[i]] (one
+// gather per adjoint call, so that spread3t_kernel's node loads are
+// contiguous and independent).
+static __global__ void __launch_bounds__(256) sort_inputs_kernel(const float2* __restrict__ fin,
+                                                          const uint32_t* __restrict__ perm, float2* __restrict__ out,
+                                                          long long N) {
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += static_cast<long long>(gridDim.x) * 256)
+        out[i] = fin[perm[i]];
 }

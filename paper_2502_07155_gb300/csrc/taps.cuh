@@ -2145,7 +2145,7 @@ __global__ void __launch_bounds__(kTapThreads) node_grad_kernel(const __grid_con
 // window has a per-tap closed form there (sinh, tabulated Shannon window, or
 // fitted polynomials); the geometry test is the column-owner kernel's.
 inline bool spread3t_applies(const TapArgs<float>& a) {
-    if (a.batch != 1 || a.wfac != nullptr) return false;
+    if (a.batch != 1 || a.wfac != nullptr || a.fsorted == nullptr) return false;
     if (a.w.poly) return true;
     return a.w.window == NFFTBL_WIN_SINH || (a.w.window == NFFTBL_WIN_TABLE && a.w.method == NFFTBL_SHANNON);
 }
@@ -2235,8 +2235,17 @@ nfftbl_status launch_tap_kernel(nfftbl_plan_s* p, const TapArgs<T>& args, int ki
         else if constexpr (D == 2) spread2_kernel<T, W><<<grid, kTapThreads, smem, p->stream>>>(args);
         else if (threads_launch != threads) {
             if constexpr (sizeof(T) == 4 && W >= 4 && W <= 16) {
-                if (tensor)
+                if (tensor) {
+                    const unsigned gb = static_cast<unsigned>(
+                        std::min<long long>((args.N + 255) / 256, 8LL * p->num_sms));
+                    if (args.N > 0) {
+                        sort_inputs_kernel<<<gb, 256, 0, p->stream>>>(
+                            reinterpret_cast<const float2*>(args.fin), args.perm,
+                            reinterpret_cast<float2*>(args.fsorted), args.N);
+                        p->launches++;
+                    }
                     spread3t_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
+                }
                 else
                     spread3c_kernel<W><<<grid, threads_launch, smem, p->stream>>>(args);
             }
