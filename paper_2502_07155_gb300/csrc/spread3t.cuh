@@ -59,8 +59,9 @@ struct Spread3T {
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int RD_WARP = 4 * NG;               // first readout warp
     static constexpr int MMA_WARP = 4 * NG + 4;
-    // stage table (floats, node-minor): g w0 as float2 [R][KS], w1 [B1][KS], w2 [B2][KS]
-    static constexpr int T0 = 0, T1 = 2 * R * KS, T2 = T1 + B1 * KS, TAB = T2 + B2 * KS;
+    // stage table (floats, node-minor): w1 [B1][KS], w2 [B2][KS]; the dimension-0
+    // values go straight into the stage's B operand
+    static constexpr int T1 = 0, T2 = B1 * KS, TAB = T2 + B2 * KS;
     static constexpr int NPAR = 12;                      // node parameters: tau[3], s[3], lb[3], g.x, g.y, pad
     static constexpr int BST = 2 * NP * KS;              // B of one stage (hi, then lo), floats
     static constexpr int BOX = R * B1 * B2;              // box cells (float2)
@@ -68,14 +69,14 @@ struct Spread3T {
     static constexpr size_t OFF_TAB = static_cast<size_t>(BOX) * 8;
     static constexpr size_t OFF_PAR = OFF_TAB + static_cast<size_t>(NG) * 2 * TAB * 4;
     static constexpr size_t OFF_B = (OFF_PAR + static_cast<size_t>(NG) * 2 * KS * NPAR * 4 + 127) / 128 * 128;
-    static constexpr size_t OFF_BAR = (OFF_B + static_cast<size_t>(NG) * BST * 4 + 127) / 128 * 128;
+    static constexpr size_t OFF_BAR = (OFF_B + static_cast<size_t>(2 * NG) * BST * 4 + 127) / 128 * 128;
     static constexpr size_t BYTES = OFF_BAR + 8 * (2 * NG + 3) + 16;
     // at least 116 KB: one block per SM, the tensor-memory allocation never waits on another block
     static constexpr size_t SMEM = BYTES > 116 * 1024 ? BYTES : 116 * 1024;
     static_assert(COLS_USED <= 512, "tensor memory holds 512 columns");
     static_assert(NP <= 256 && NP % 16 == 0, "MMA N for M = 128");
     static_assert(NT * 128 >= ROWS, "M tiles cover the rows");
-    static_assert(BOX % 2 == 0 && (TAB * 4) % 16 == 0 && (T1 * 4) % 16 == 0 && (T2 * 4) % 16 == 0, "alignment");
+    static_assert(BOX % 2 == 0 && (TAB * 4) % 16 == 0 && (T2 * 4) % 16 == 0 && (BST * 4) % 16 == 0, "alignment");
 };
 
 // ---- tcgen05 / tensor-memory helpers (sm_100 family PTX) -------------------
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                         ok = wait_or_abort(dempty, static_cast<uint32_t>((seg - 1) & 1), s_abort, a.err, a.wait_ns);
                     if (ok) {
                         tc_fence_after();
-                        const float* bh = s_b + static_cast<size_t>(b) * G::BST;
+                        const float* bh = s_b + static_cast<size_t>(2 * b + ((S / G::NG) & 1)) * G::BST;
                         const uint64_t dh = smem_desc_noswz(bh, 128, 256);
                         const uint64_t dl = smem_desc_noswz(bh + G::NP * G::KS, 128, 256);
 #pragma unroll 1
@@ -393,10 +394,18 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                 if (pt == 0) pg = a.fsorted[i];
             }
         };
+        // clear a stage's table (dimensions 1, 2) and B (hi, lo) of this group
+        auto clear_stage = [&](int buf) {
+            float4* t4 = reinterpret_cast<float4*>(s_tab + static_cast<size_t>(grp * 2 + buf) * G::TAB);
+            for (int idx = gt; idx < G::TAB / 4; idx += 128) t4[idx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4* b4 = reinterpret_cast<float4*>(s_b + static_cast<size_t>(2 * grp + buf) * G::BST);
+            for (int idx = gt; idx < G::BST / 4; idx += 128) b4[idx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        };
         int tb = 0;
         StageRef cur;
         first_of(blockIdx.x, 0, cur);
         prefetch(cur);
+        clear_stage(0);
         while (cur.item < a.n_work) {
             const long long S = cur.S0 + cur.s;
             float* par = s_par + static_cast<size_t>(grp * 2 + tb) * G::KS * G::NPAR;
@@ -427,20 +436,31 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                 }
             }
             named_sync(1 + grp, 128);
-            // window values per box position (zero outside each node's taps)
-            constexpr int E = G::KS * (G::R + G::B1 + G::B2);
-            for (int e = gt; e < E; e += 128) {
-                const int k = e & (G::KS - 1), pe = e / G::KS;   // node, position entry
-                const int t = pe < G::R ? 0 : pe < G::R + G::B1 ? 1 : 2;
-                const int pos = pe - (t == 0 ? 0 : t == 1 ? G::R : G::R + G::B1);
+            // the 2m window values of every (node, dimension): dimensions 1 and 2 into
+            // the table at their box positions, dimension 0 times the input value
+            // into B (hi, lo); every other entry was cleared beforehand
+            float* bh = s_b + static_cast<size_t>(2 * grp + tb) * G::BST;
+            for (int e = gt; e < 3 * G::KS * W; e += 128) {
+                const int tap = e % W, kt = e / W, t = kt / G::KS, k = kt - t * G::KS;
                 const float* pp = par + k * G::NPAR;
-                const int tap = pos - __float_as_int(pp[6 + t]);
-                float w = 0.0f;
-                if (tap >= 0 && tap < W) w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
-                if (t == 0)
-                    reinterpret_cast<float2*>(tab + G::T0)[pos * G::KS + k] = make_float2(pp[9] * w, pp[10] * w);
-                else
-                    tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
+                const int lb = __float_as_int(pp[6 + t]);
+                if (lb >= 0) {   // (no node: lb = -1000)
+                    const float w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
+                    const int pos = lb + tap;
+                    if (t == 0) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const float v = pp[9 + c] * w;
+                            const float h = tf32_round(v);
+                            const int n = 2 * pos + c;
+                            const int off = (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+                            bh[off] = h;
+                            bh[G::NP * G::KS + off] = v - h;
+                        }
+                    } else {
+                        tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
+                    }
+                }
             }
             named_sync(1 + grp, 128);
             StageRef nxt;
@@ -449,6 +469,8 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
             if (S >= G::NG)
                 wait_or_abort(&empty[grp], static_cast<uint32_t>(((S / G::NG) - 1) & 1), s_abort, a.err, a.wait_ns);
             tc_fence_after();
+            // the group's other buffers (its previous stage's, whose MMAs are done) cleared for its next stage
+            clear_stage(tb ^ 1);
             // A = w1[i1] w2[i2] for the stage's eight nodes, hi and lo
             const uint32_t col = static_cast<uint32_t>(G::COL_A + grp * G::A_COLS);
 #pragma unroll
@@ -459,27 +481,23 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                 const float4* p1 = reinterpret_cast<const float4*>(tab + G::T1 + i1 * G::KS);
                 const float4* p2 = reinterpret_cast<const float4*>(tab + G::T2 + i2 * G::KS);
                 const float4 x0 = p1[0], x1 = p1[1], y0 = p2[0], y1 = p2[1];
+                float2 av[4] = {__fmul2_rn(make_float2(x0.x, x0.y), make_float2(y0.x, y0.y)),
+                                __fmul2_rn(make_float2(x0.z, x0.w), make_float2(y0.z, y0.w)),
+                                __fmul2_rn(make_float2(x1.x, x1.y), make_float2(y1.x, y1.y)),
+                                __fmul2_rn(make_float2(x1.z, x1.w), make_float2(y1.z, y1.w))};
                 float hi[8], lo[8];
-                const float av[8] = {x0.x * y0.x, x0.y * y0.y, x0.z * y0.z, x0.w * y0.w,
-                                     x1.x * y1.x, x1.y * y1.y, x1.z * y1.z, x1.w * y1.w};
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float v = in ? av[u] : 0.0f;
-                    hi[u] = tf32_round(v);
-                    lo[u] = v - hi[u];
+                for (int u = 0; u < 4; ++u) {
+                    const float2 v = in ? av[u] : make_float2(0.0f, 0.0f);
+                    const float2 h = make_float2(tf32_round(v.x), tf32_round(v.y));
+                    const float2 l = __ffma2_rn(h, make_float2(-1.0f, -1.0f), v);   // v - h, exact
+                    hi[2 * u] = h.x;
+                    hi[2 * u + 1] = h.y;
+                    lo[2 * u] = l.x;
+                    lo[2 * u + 1] = l.y;
                 }
                 tmem_st8(lane_base + col + static_cast<uint32_t>(t * G::KS), hi);
                 tmem_st8(lane_base + col + static_cast<uint32_t>((G::NT + t) * G::KS), lo);
-            }
-            // B = (g w0)[(i0, c)] of the stage's eight nodes, K-major core matrices of 8 x 4
-            float* bh = s_b + static_cast<size_t>(grp) * G::BST;
-            for (int idx = gt; idx < G::NP * G::KS; idx += 128) {
-                const int n = idx / G::KS, kk = idx - n * G::KS;
-                const float v = n < 2 * G::R ? tab[G::T0 + (n >> 1) * 2 * G::KS + 2 * kk + (n & 1)] : 0.0f;
-                const float h = tf32_round(v);
-                const int off = (n >> 3) * 64 + (kk >> 2) * 32 + (n & 7) * 4 + (kk & 3);
-                bh[off] = h;
-                bh[G::NP * G::KS + off] = v - h;
             }
             tmem_wait_st();
             fence_async_shared();
