@@ -49,8 +49,11 @@ struct Spread3T {
     static constexpr int NP = (2 * R + 15) / 16 * 16;    // GEMM columns (i0, re/im), padded
     static constexpr int KS = 8;                         // nodes per stage (one K step)
     static constexpr int NG = 3;                         // producer groups = stage buffers
+    // accumulators: two where tensor memory holds them (m <= 6), so that the
+    // readout of one segment overlaps the MMAs of the next
+    static constexpr int ND = W <= 12 ? 2 : 1;
     static constexpr int RO = 16;                        // stages per accumulator segment
-    static constexpr int COL_A = NT * NP;                // tensor-memory columns: accumulator first
+    static constexpr int COL_A = ND * NT * NP;           // tensor-memory columns: accumulators first
     static constexpr int A_COLS = 2 * NT * KS;           // A hi and lo of one stage
     static constexpr int COLS_USED = COL_A + NG * A_COLS;
     static constexpr int TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
@@ -70,7 +73,7 @@ struct Spread3T {
     static constexpr size_t OFF_PAR = OFF_TAB + static_cast<size_t>(NG) * 2 * TAB * 4;
     static constexpr size_t OFF_B = (OFF_PAR + static_cast<size_t>(NG) * 2 * KS * NPAR * 4 + 127) / 128 * 128;
     static constexpr size_t OFF_BAR = (OFF_B + static_cast<size_t>(2 * NG) * BST * 4 + 127) / 128 * 128;
-    static constexpr size_t BYTES = OFF_BAR + 8 * (2 * NG + 3) + 16;
+    static constexpr size_t BYTES = OFF_BAR + 8 * (2 * NG + 2 * ND + 1) + 16;
     // at least 116 KB: one block per SM, the tensor-memory allocation never waits on another block
     static constexpr size_t SMEM = BYTES > 116 * 1024 ? BYTES : 116 * 1024;
     static_assert(COLS_USED <= 512, "tensor memory holds 512 columns");
@@ -230,9 +233,9 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
     float* s_b = reinterpret_cast<float*>(smem + G::OFF_B);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);   // [NG], 128 arrivals
     uint64_t* empty = full + G::NG;                                     // [NG], one commit
-    uint64_t* dfull = empty + G::NG;                                    // segment accumulated (commit)
-    uint64_t* dempty = dfull + 1;                                       // segment read (128 arrivals)
-    uint64_t* fin = dempty + 1;                                         // final drain (commit)
+    uint64_t* dfull = empty + G::NG;                                    // [ND] segment accumulated (commit)
+    uint64_t* dempty = dfull + G::ND;                                   // [ND] segment read (128 arrivals)
+    uint64_t* fin = dempty + G::ND;                                     // final drain (commit)
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -245,8 +248,10 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
             mbar_init(&full[b], 128);
             mbar_init(&empty[b], 1);
         }
-        mbar_init(dfull, 1);
-        mbar_init(dempty, 128);
+        for (int b = 0; b < G::ND; ++b) {
+            mbar_init(&dfull[b], 1);
+            mbar_init(&dempty[b], 128);
+        }
         mbar_init(fin, 1);
         *s_abort = 0;
         fence_mbar_init();
@@ -272,8 +277,9 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                     const int b = static_cast<int>(S % G::NG);
                     const bool first = (s % G::RO) == 0, last = (s % G::RO) == G::RO - 1 || s == ns - 1;
                     bool ok = wait_or_abort(&full[b], static_cast<uint32_t>((S / G::NG) & 1), s_abort, a.err, a.wait_ns);
-                    if (ok && first && seg > 0)
-                        ok = wait_or_abort(dempty, static_cast<uint32_t>((seg - 1) & 1), s_abort, a.err, a.wait_ns);
+                    if (ok && first && seg >= G::ND)   // the accumulator's previous segment has been read
+                        ok = wait_or_abort(&dempty[seg % G::ND], static_cast<uint32_t>((seg / G::ND - 1) & 1), s_abort,
+                                           a.err, a.wait_ns);
                     if (ok) {
                         tc_fence_after();
                         const float* bh = s_b + static_cast<size_t>(2 * b + ((S / G::NG) & 1)) * G::BST;
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                         const uint64_t dl = smem_desc_noswz(bh + G::NP * G::KS, 128, 256);
 #pragma unroll 1
                         for (int t = 0; t < G::NT; ++t) {
-                            const uint32_t d = tbase + static_cast<uint32_t>(t * G::NP);
+                            const uint32_t d = tbase + static_cast<uint32_t>(((seg % G::ND) * G::NT + t) * G::NP);
                             const uint32_t ah = tbase + static_cast<uint32_t>(G::COL_A + b * G::A_COLS + t * G::KS);
                             const uint32_t al = ah + static_cast<uint32_t>(G::NT * G::KS);
                             mma_tf32_ts(d, ah, dh, kIdesc, first ? 0u : 1u);
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                         }
                         issued = true;
                         mma_commit(&empty[b]);
-                        if (last) mma_commit(dfull);
+                        if (last) mma_commit(&dfull[seg % G::ND]);
                     }
                     if (last) ++seg;
                 }
@@ -310,7 +316,8 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
             const int ns = max(1, (a.work[item].count + G::KS - 1) / G::KS);
             const int nseg = (ns + G::RO - 1) / G::RO;
             for (int sg = 0; sg < nseg; ++sg, ++seg) {
-                wait_or_abort(dfull, static_cast<uint32_t>(seg & 1), s_abort, a.err, a.wait_ns);
+                const int db = seg % G::ND;
+                wait_or_abort(&dfull[db], static_cast<uint32_t>((seg / G::ND) & 1), s_abort, a.err, a.wait_ns);
                 tc_fence_after();
 #pragma unroll 1
                 for (int t = 0; t < G::NT; ++t) {
@@ -319,7 +326,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
 #pragma unroll 1
                     for (int c0 = 0; c0 < G::NP; c0 += 16) {
                         float v[16];
-                        tmem_ld16(lane_base + static_cast<uint32_t>(t * G::NP + c0), v);
+                        tmem_ld16(lane_base + static_cast<uint32_t>((db * G::NT + t) * G::NP + c0), v);
                         if (r < G::ROWS) {
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(dempty);
+                mbar_arrive(&dempty[db]);
             }
             // the item's box into its slot of the ordered flush
             named_sync(1 + G::NG, 128);
