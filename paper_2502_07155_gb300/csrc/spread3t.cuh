@@ -20,7 +20,7 @@
 // accumulations inside the tensor core drift measurably at the dense
 // centre of a spoke workload (a million contributions to a cell).
 //
-// Warp roles (17 warps):
+// Warp roles (21 warps):
 //  - three producer groups of four warps; group g builds the stages S with
 //    S mod 3 = g into stage buffer g: node parameters, the stage's window
 //    values per box position (node-minor tables, zero outside each node's
@@ -30,7 +30,7 @@
 //  - one MMA warp: its elected thread issues the stage's 3 x (M tiles) MMAs
 //    and commits them to the buffer's "empty" barrier, and to "dfull" after
 //    the last stage of a segment (at most RO stages of one item);
-//  - one readout group of four warps: after each segment it adds the
+//  - one readout group of eight warps: after each segment it adds the
 //    accumulator into the shared box, and after an item's last segment it
 //    copies the box to the item's slot of the ordered flush (gather_kernel).
 //
@@ -58,10 +58,11 @@ struct Spread3T {
     static constexpr int COLS_USED = COL_A + NG * A_COLS;
     static constexpr int TCOLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
                                  : COLS_USED <= 256 ? 256 : 512;
-    static constexpr int WARPS = 4 * NG + 4 + 1;         // producers, readout, MMA
+    static constexpr int RDW = 8;                        // readout warps (two per lane quarter)
+    static constexpr int WARPS = 4 * NG + RDW + 1;       // producers, readout, MMA
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int RD_WARP = 4 * NG;               // first readout warp
-    static constexpr int MMA_WARP = 4 * NG + 4;
+    static constexpr int MMA_WARP = 4 * NG + RDW;
     // stage table (floats, node-minor): w1 [B1][KS], w2 [B2][KS]; the dimension-0
     // values go straight into the stage's B operand
     static constexpr int T1 = 0, T2 = B1 * KS, TAB = T2 + B2 * KS;
@@ -198,6 +199,20 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
                  : "memory");
 }
 
+// Eight consecutive 32-bit columns of this thread's lane (waited for in the
+// same statement).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 // Sixteen consecutive 32-bit columns of this thread's lane (waited for in
 // the same statement).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -234,7 +249,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);   // [NG], 128 arrivals
     uint64_t* empty = full + G::NG;                                     // [NG], one commit
     uint64_t* dfull = empty + G::NG;                                    // [ND] segment accumulated (commit)
-    uint64_t* dempty = dfull + G::ND;                                   // [ND] segment read (128 arrivals)
+    uint64_t* dempty = dfull + G::ND;                                   // [ND] segment read (readout arrivals)
     uint64_t* fin = dempty + G::ND;                                     // final drain (commit)
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
@@ -250,7 +265,7 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
         }
         for (int b = 0; b < G::ND; ++b) {
             mbar_init(&dfull[b], 1);
-            mbar_init(&dempty[b], 128);
+            mbar_init(&dempty[b], 32 * G::RDW);
         }
         mbar_init(fin, 1);
         *s_abort = 0;
@@ -308,8 +323,9 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
         }
         __syncwarp();
     } else if (warp >= G::RD_WARP) {
-        // ---------------- readout group: accumulator segments into the shared box
-        const int q = warp & 3, rt = tid - 32 * G::RD_WARP;   // lane quarter, thread of the group
+        // ---------------- readout group: accumulator segments into the shared box; warp
+        // (quarter q, half h) reads the lanes of quarter q and the 8-column chunks h, h + 2, ...
+        const int q = warp & 3, h = (warp - G::RD_WARP) >> 2, rt = tid - 32 * G::RD_WARP;
         const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * q) << 16);
         int seg = 0;
         for (int item = blockIdx.x; item < a.n_work; item += gridDim.x) {
@@ -324,21 +340,17 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                     const int r = 128 * t + 32 * q + lane;
                     const int i1 = r / G::B2, i2 = r - (r / G::B2) * G::B2;
 #pragma unroll 1
-                    for (int c0 = 0; c0 < G::NP; c0 += 16) {
-                        float v[16];
-                        tmem_ld16(lane_base + static_cast<uint32_t>((db * G::NT + t) * G::NP + c0), v);
+                    for (int c0 = 8 * h; c0 < G::NP; c0 += 16) {
+                        float v[8];
+                        tmem_ld8(lane_base + static_cast<uint32_t>((db * G::NT + t) * G::NP + c0), v);
                         if (r < G::ROWS) {
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
+                            for (int u = 0; u < 4; ++u) {
                                 const int i0 = c0 / 2 + u;
                                 if (i0 < G::R) {
                                     float2* cell = s_box + (i0 * G::B1 + i1) * G::B2 + i2;
-                                    if (sg == 0) {
-                                        *cell = make_float2(v[2 * u], v[2 * u + 1]);
-                                    } else {
-                                        const float2 o = *cell;
-                                        *cell = make_float2(o.x + v[2 * u], o.y + v[2 * u + 1]);
-                                    }
+                                    const float2 x = make_float2(v[2 * u], v[2 * u + 1]);
+                                    *cell = (sg == 0) ? x : __fadd2_rn(*cell, x);
                                 }
                             }
                         }
@@ -348,11 +360,11 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
                 mbar_arrive(&dempty[db]);
             }
             // the item's box into its slot of the ordered flush
-            named_sync(1 + G::NG, 128);
+            named_sync(1 + G::NG, 32 * G::RDW);
             const float4* src = reinterpret_cast<const float4*>(s_box);
             float4* dst = reinterpret_cast<float4*>(a.part + static_cast<long long>(item) * G::BOX);
-            for (int idx = rt; idx < G::BOX / 2; idx += 128) dst[idx] = src[idx];
-            named_sync(1 + G::NG, 128);
+            for (int idx = rt; idx < G::BOX / 2; idx += 32 * G::RDW) dst[idx] = src[idx];
+            named_sync(1 + G::NG, 32 * G::RDW);
         }
     } else {
         // ---------------- producer group grp: stages S with S mod NG = grp
