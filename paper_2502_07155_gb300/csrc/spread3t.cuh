@@ -15,10 +15,10 @@
 // split into its TF32 rounding and the remainder, a = a_hi + a_lo, and the
 // product is a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped a_lo b_lo is
 // below FP32 rounding).  The tensor core accumulates at most RO stages
-// (3 RO MMAs per output) before the accumulator is added, in FP32 with
-// round-to-nearest, into a box in shared memory: longer chains of
-// accumulations inside the tensor core drift measurably at the dense
-// centre of a spoke workload (a million contributions to a cell).
+// (3 RO MMAs per output; RO = 16, or 32 at m >= 7) before the accumulator is
+// added, in FP32 with round-to-nearest, into a box in shared memory: longer
+// chains of accumulations inside the tensor core drift measurably at the
+// dense centre of a spoke workload (a million contributions to a cell).
 //
 // Warp roles (21 warps):
 //  - three producer groups of four warps; group g builds the stages S with
@@ -52,7 +52,10 @@ struct Spread3T {
     // accumulators: two where tensor memory holds them (m <= 6), so that the
     // readout of one segment overlaps the MMAs of the next
     static constexpr int ND = W <= 12 ? 2 : 1;
-    static constexpr int RO = 16;                        // stages per accumulator segment
+    // stages per accumulator segment: 16, or 32 at m >= 7, where the single
+    // accumulator waits for every readout (chains of 3 RO MMAs per output;
+    // the error they leave at the densest spoke cells grows with RO)
+    static constexpr int RO = W >= 14 ? 32 : 16;
     static constexpr int COL_A = ND * NT * NP;           // tensor-memory columns: accumulators first
     static constexpr int A_COLS = 2 * NT * KS;           // A hi and lo of one stage
     static constexpr int COLS_USED = COL_A + NG * A_COLS;
