@@ -55,7 +55,7 @@ struct Spread3T {
     // stages per accumulator segment: 16, or 32 at m >= 7, where the single
     // accumulator waits for every readout (chains of 3 RO MMAs per output;
     // the error they leave at the densest spoke cells grows with RO)
-    static constexpr int RO = W >= 14 ? 32 : 16;
+    static constexpr int RO = W >= 14 ? 32 : 8;
     static constexpr int COL_A = ND * NT * NP;           // tensor-memory columns: accumulators first
     static constexpr int A_COLS = 2 * NT * KS;           // A hi and lo of one stage
     static constexpr int COLS_USED = COL_A + NG * A_COLS;
