@@ -29,7 +29,7 @@ def built():
 
 @pytest.mark.parametrize("d,prec", [(2, "f32"), (3, "f32"), (3, "f64")])
 def test_wait_runs_out_and_plan_recovers(d, prec):
-    M, m = {2: (64, 6), 3: (32, 4)}[d]
+    M, m = {2: (64, 6), 3: (32, 7)}[d]   # (d = 3 FP32, m = 7: the two-buffer interpolation)
     N = 3000
     rdt, cdt = (np.float64, np.complex128) if prec == "f64" else (np.float32, np.complex64)
     plan = nb.Plan(d, M, 2.0, m, precision=prec)
