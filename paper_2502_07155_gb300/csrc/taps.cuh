@@ -993,7 +993,7 @@ __device__ __forceinline__ bool stage_box(const CUtensorMap* tmap, const TapArgs
         }
         const bool ok = mbar_wait_bounded(bar, phase, a.err, a.wait_ns);
         phase ^= 1u;
-        return __syncthreads_and(ok) != 0;   // one verdict for the whole block
+        return __syncthreads_and(ok) != 0;   // one decision for the whole block
     }
     // periodic wrap (classical NFFT tiles crossing the grid edge): plain loads
     for (int idx = threadIdx.x; idx < nb * box_cells; idx += blockDim.x) {
@@ -1194,7 +1194,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) interp3p_kernel(const __grid_
     for (int item = blockIdx.x; item < a.n_work; item += gridDim.x, ++k) {
         const int buf = k & 1;
         const bool landed = mbar_wait_bounded(&full[buf], static_cast<uint32_t>((k >> 1) & 1), a.err, a.wait_ns);
-        if (!__all_sync(0xffffffffu, landed)) break;   // one verdict per warp
+        if (!__all_sync(0xffffffffu, landed)) break;   // one decision per warp
         const WorkItem wi = a.work[item];
         int org[3] = {0, 0, 0};
         tile_origin<3>(a.g, wi.tile, false, org);
