@@ -1147,7 +1147,7 @@ __global__ void __launch_bounds__(kTapThreads) interp_kernel(const __grid_consta
 // warp to leave an item refills its buffer with the item two ahead.  Every
 // wait is bounded; a block whose wait ran out stops taking work, waits for
 // the copies it issued, and returns (the error flag is set).
-constexpr int kPipeThreads = 512;
+constexpr int kPipeThreads = 384;
 
 template <int W>
 __global__ void __launch_bounds__(kPipeThreads, 1) interp3p_kernel(const __grid_constant__ CUtensorMap tmap,
