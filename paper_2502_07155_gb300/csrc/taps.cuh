@@ -741,7 +741,7 @@ __device__ __forceinline__ C2<T> contract_lazy0(const C2<T>* __restrict__ box, c
 // value is loaded once and enters both nodes' sums, which halves the
 // shared-memory traffic of the pair.  Node b's arithmetic is node a's with
 // its own weights, so each result equals contract_lazy0 of that node alone.
-template <typename T, int D, int W, int WK, bool COMP = false>
+template <typename T, int D, int W, int WK, bool COMP = false, int UB = 2>
 __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ box, const TileGeom& g,
                                                     const int (&lb)[3], T tau0a, T s0a, const T (&w1a)[TapN<W>::A],
                                                     const T (&w2a)[TapN<W>::A], T tau0b, T s0b,
@@ -785,8 +785,7 @@ __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ bo
             const T w0a = fast_weight<T, WK>(tau0a, s0a, a, m, wp);
             const T w0b = fast_weight<T, WK>(tau0b, s0b, a, m, wp);
             C2<T> mida = cmake<T>(T(0), T(0)), midb = cmake<T>(T(0), T(0));
-#pragma unroll 2
-            for (int b = 0; b < nw; ++b) {
+            auto brow = [&](int b) {
                 const C2<T>* row = p + a * p0 + b * p1;
                 C2<T> ra = cmake<T>(T(0), T(0)), rb = cmake<T>(T(0), T(0));
 #pragma unroll
@@ -805,6 +804,14 @@ __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ bo
                     mida = cfma(ra, w1a[b], mida);
                     midb = cfma(rb, w1b[b], midb);
                 }
+            };
+            // (UB: rows in flight; 4 where the kernel has the registers for them)
+            if constexpr (UB == 4) {
+#pragma unroll 4
+                for (int b = 0; b < nw; ++b) brow(b);
+            } else {
+#pragma unroll 2
+                for (int b = 0; b < nw; ++b) brow(b);
             }
             if constexpr (!COMP) {
                 acca = cfma(mida, w0a, acca);
@@ -824,7 +831,7 @@ __device__ __forceinline__ void contract_lazy0_pair(const C2<T>* __restrict__ bo
 // The inline-weight interpolation of a pair head: nodes ia and ib (= ia
 // when the head has no partner) of one cell, weights of dimensions 1 .. d-1
 // in registers, dimension-0 weights evaluated per row.
-template <typename T, int D, int W, int WK>
+template <typename T, int D, int W, int WK, int UB = 2>
 __device__ __forceinline__ void interp_pair(const TapArgs<T>& a, const C2<T>* box, const int (&lb)[3],
                                             const T (&taua)[3], const T (&taub)[3], int nw, C2<T>& fa, C2<T>& fb) {
     constexpr int A = TapN<W>::A;
@@ -838,10 +845,11 @@ __device__ __forceinline__ void interp_pair(const TapArgs<T>& a, const C2<T>* bo
     const T s0a = (WK == WK_CSINH) ? T(0) : (WK == WK_SINH) ? kind_sin<T, WK_SINH>(taua[0], a.w) : FM<T>::sinpi(taua[0]);
     const T s0b = (WK == WK_CSINH) ? T(0) : (WK == WK_SINH) ? kind_sin<T, WK_SINH>(taub[0], a.w) : FM<T>::sinpi(taub[0]);
     if (a.comp)
-        contract_lazy0_pair<T, D, W, WK, true>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w, nw,
-                                               fa, fb);
+        contract_lazy0_pair<T, D, W, WK, true, UB>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w,
+                                                   nw, fa, fb);
     else
-        contract_lazy0_pair<T, D, W, WK>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w, nw, fa, fb);
+        contract_lazy0_pair<T, D, W, WK, false, UB>(box, a.g, lb, taua[0], s0a, w1a, w2a, taub[0], s0b, w1b, w2b, a.w,
+                                                    nw, fa, fb);
 }
 
 // The inline-weight interpolation of one node (FP64 plans): weights of
@@ -1055,7 +1063,7 @@ __global__ void __launch_bounds__(256) factor_kernel(const TapArgs<T> a, T* __re
 
 // One thread's share of interp_kernel: head hv (bit 31: the next sorted node
 // is its same-cell partner) of a staged box, batch entries b0 .. b0+nb-1.
-template <typename T, int D, int W>
+template <typename T, int D, int W, int UB = 2>
 __device__ __forceinline__ void interp_head(const TapArgs<T>& a, const C2<T>* box, int slot, const int (&org)[3],
                                             uint32_t hv, int b0, int nb, int wk, int nw, int m) {
     const long long ia = static_cast<long long>(hv & 0x7FFFFFFFu);
@@ -1072,9 +1080,9 @@ __device__ __forceinline__ void interp_head(const TapArgs<T>& a, const C2<T>* bo
         const int wkc = closed_kind(a.w);
         if (!a.wfac && nb == 1 && (wkc == WK_SINH || wkc == WK_CSINH || wkc == WK_TABLE)) {
             C2<T> fa, fb;
-            if (wkc == WK_SINH) interp_pair<T, D, W, WK_SINH>(a, box, lb, taua, taub, nw, fa, fb);
-            else if (wkc == WK_CSINH) interp_pair<T, D, W, WK_CSINH>(a, box, lb, taua, taub, nw, fa, fb);
-            else interp_pair<T, D, W, WK_TABLE>(a, box, lb, taua, taub, nw, fa, fb);
+            if (wkc == WK_SINH) interp_pair<T, D, W, WK_SINH, UB>(a, box, lb, taua, taub, nw, fa, fb);
+            else if (wkc == WK_CSINH) interp_pair<T, D, W, WK_CSINH, UB>(a, box, lb, taua, taub, nw, fa, fb);
+            else interp_pair<T, D, W, WK_TABLE, UB>(a, box, lb, taua, taub, nw, fa, fb);
             a.fout[static_cast<long long>(b0) * a.N + da] = fa;
             if (two) a.fout[static_cast<long long>(b0) * a.N + db] = fb;
             return;
@@ -1206,7 +1214,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) interp3p_kernel(const __grid_
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= nh) break;
             const int h = base + lane;
-            if (h < nh) interp_head<float, 3, W>(a, box, slot, org, a.heads[wi.start + h], 0, 1, wk, nw, m);
+            if (h < nh) interp_head<float, 3, W, 4>(a, box, slot, org, a.heads[wi.start + h], 0, 1, wk, nw, m);
         }
         __syncwarp();
         if (lane == 0) {
