@@ -232,12 +232,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// One tap weight of a closed-form kind (s: the kind's sine of the node).
-__device__ __forceinline__ float s3t_weight(int wk, float tau, float s, int a, int m, const WinParams<float>& wp) {
-    if (wk == WK_SINH) return fast_weight<float, WK_SINH>(tau, s, a, m, wp);
-    if (wk == WK_TABLE) return fast_weight<float, WK_TABLE>(tau, s, a, m, wp);
-    if (wk == WK_CSINH) return fast_weight<float, WK_CSINH>(tau, s, a, m, wp);
-    return fast_weight<float, WK_POLY>(tau, s, a, m, wp);
+// The 2m window values of every (node, dimension) of a stage, weight kind
+// WKC fixed at compile time: dimensions 1 and 2 into the stage table at their
+// box positions, dimension 0 times the node's input value into B (hi, lo);
+// thread gt of the producer group takes every 128th entry.
+template <int W, int WKC>
+__device__ __forceinline__ void spread3t_entries(const TapArgs<float>& a, const float* par, float* tab, float* bh,
+                                                 int gt) {
+    using G = Spread3T<W>;
+    constexpr int m = W / 2;
+    for (int e = gt; e < 3 * G::KS * W; e += 128) {
+        const int tap = e % W, kt = e / W, t = kt / G::KS, k = kt - t * G::KS;
+        const float* pp = par + k * G::NPAR;
+        const int lb = __float_as_int(pp[6 + t]);
+        if (lb >= 0) {   // (no node: lb = -1000)
+            const float w = fast_weight<float, WKC>(pp[t], pp[3 + t], tap, m, a.w);
+            const int pos = lb + tap;
+            if (t == 0) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float v = pp[9 + c] * w;
+                    const float h = tf32_round(v);
+                    const int n = 2 * pos + c;
+                    const int off = (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
+                    bh[off] = h;
+                    bh[G::NP * G::KS + off] = v - h;
+                }
+            } else {
+                tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
+            }
+        }
+    }
 }
 
 template <int W>
@@ -462,28 +487,10 @@ __global__ void __launch_bounds__(Spread3T<W>::THREADS, 1) spread3t_kernel(const
             // the table at their box positions, dimension 0 times the input value
             // into B (hi, lo); every other entry was cleared beforehand
             float* bh = s_b + static_cast<size_t>(2 * grp + tb) * G::BST;
-            for (int e = gt; e < 3 * G::KS * W; e += 128) {
-                const int tap = e % W, kt = e / W, t = kt / G::KS, k = kt - t * G::KS;
-                const float* pp = par + k * G::NPAR;
-                const int lb = __float_as_int(pp[6 + t]);
-                if (lb >= 0) {   // (no node: lb = -1000)
-                    const float w = s3t_weight(wk, pp[t], pp[3 + t], tap, m, a.w);
-                    const int pos = lb + tap;
-                    if (t == 0) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const float v = pp[9 + c] * w;
-                            const float h = tf32_round(v);
-                            const int n = 2 * pos + c;
-                            const int off = (n >> 3) * 64 + (k >> 2) * 32 + (n & 7) * 4 + (k & 3);
-                            bh[off] = h;
-                            bh[G::NP * G::KS + off] = v - h;
-                        }
-                    } else {
-                        tab[(t == 1 ? G::T1 : G::T2) + pos * G::KS + k] = w;
-                    }
-                }
-            }
+            if (wk == WK_SINH) spread3t_entries<W, WK_SINH>(a, par, tab, bh, gt);
+            else if (wk == WK_CSINH) spread3t_entries<W, WK_CSINH>(a, par, tab, bh, gt);
+            else if (wk == WK_TABLE) spread3t_entries<W, WK_TABLE>(a, par, tab, bh, gt);
+            else spread3t_entries<W, WK_POLY>(a, par, tab, bh, gt);
             named_sync(1 + grp, 128);
             StageRef nxt;
             next_of(cur, nxt);
