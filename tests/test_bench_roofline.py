@@ -49,3 +49,54 @@ def test_hbm_bound_when_the_grid_dominates():
     r = bench.short_sum_roofline(1, 2, 1 << 10, 1, 1 << 22, 1e-3)
     assert r["bound_unit"] == "hbm" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert max(r["t_bound_us"], key=r["t_bound_us"].get) == "hbm"
+
+
+def test_tensor_spreading_stage_count_by_direct_binning():
+    """The tensor-pipe figure of the d = 3 spreading counts its stages: per
+    work item (8^3-cell tile of L = 2M, at most 1024 nodes) ceil(nodes / 8)
+    stages, each (M tiles) x 3 TF32 MMAs of 128 x N_P x 8.  Checked against
+    the tiles and items counted one node at a time."""
+    import numpy as np
+    rng = np.random.default_rng(4)
+    M, m = 32, 8
+    L = 2 * M
+    x = rng.uniform(-0.5, 0.5, size=(6000, 3)).astype(np.float32)
+    x[:2500] = np.float32(0.01)                                        # one tile of 2500 nodes: 3 items
+    per_tile = {}
+    for p in x:
+        cell = [int(np.floor(np.float32(L) * p[t])) + L // 2 for t in range(3)]
+        key = tuple(c // 8 for c in cell)
+        per_tile[key] = per_tile.get(key, 0) + 1
+    stages = 0
+    for n in per_tile.values():
+        while n > 0:
+            k = min(n, 1024)
+            stages += (k + 7) // 8
+            n -= k
+    r = bench.tensor_spread_roofline(x, M, m, 1e-3)
+    assert r["stages"] == stages
+    W = 2 * m
+    R, B2 = 8 + W - 1, 8 + W
+    NT, NP = (R * B2 + 127) // 128, (2 * R + 15) // 16 * 16
+    assert (NT, NP) == (5, 48)
+    assert r["mma_flops_per_launch"] == stages * NT * 3 * 128 * NP * 8 * 2
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+
+
+def test_traffic_rows_follow_the_source_digest(tmp_path, monkeypatch):
+    """A traffic row is reported only while its digest matches the current
+    short-sum kernel source; any change to the source makes the key null."""
+    import hashlib
+    src = tmp_path / "paper_2502_07155_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (src / "taps.cuh").write_bytes(b"// kernels\n")
+    dig = hashlib.sha256(b"// kernels\n").hexdigest()[:12]
+    (tmp_path / "profiles" / "traffic.md").write_text(
+        "| workload | kernel | bytes | digest |\n|---|---|---|---|\n"
+        f"| d2_M256_m8_N2^20 | spread | 123 | {dig} |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("d2_M256_m8_N2^20", "spread") == 123
+    assert bench.traffic_from_profiles("d2_M256_m8_N2^20", "interp") is None
+    (src / "taps.cuh").write_bytes(b"// kernels, changed\n")
+    assert bench.traffic_from_profiles("d2_M256_m8_N2^20", "spread") is None
